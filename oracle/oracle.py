@@ -1,0 +1,249 @@
+"""ctypes front end of the FP64 CPU oracle (``panna_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py``.  The product path never imports it.
+
+The shared library is compiled from the single C file with the system C compiler the
+first time it is needed (or by :func:`build`) into ``oracle/_build/``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "panna_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libpanna_oracle.so")
+MAXL = 8
+
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+_i32p = C.POINTER(C.c_int32)
+_u8p = C.POINTER(C.c_uint8)
+
+
+class OrcDesc(C.Structure):
+    _fields_ = [("n_species", C.c_int), ("rc", C.c_double),
+                ("n_rad", C.c_int), ("rs_rad", _dp), ("eta_rad", C.c_double),
+                ("n_ang_r", C.c_int), ("rs_ang", _dp),
+                ("n_theta", C.c_int), ("theta_s", _dp),
+                ("eta_ang", C.c_double), ("zeta", C.c_double), ("eps_theta", C.c_double)]
+
+
+class OrcArch(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("widths", C.c_int * (MAXL + 1)), ("act", C.c_int * MAXL)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, IEEE double, no fast-math) if it is missing or stale."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+                               "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        L.orc_descriptor_size.restype = C.c_int
+        L.orc_descriptor_size.argtypes = [C.POINTER(OrcDesc)]
+        L.orc_center.restype = None
+        L.orc_center.argtypes = [C.POINTER(OrcDesc), C.c_int, _dp, _i32p, _dp, _dp]
+        L.orc_mlp.restype = None
+        L.orc_mlp.argtypes = [C.POINTER(OrcArch), _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double, _dp]
+        L.orc_neighbor_list.restype = C.c_int64
+        L.orc_neighbor_list.argtypes = [C.c_int64, _i64p, _dp, _dp, _u8p, C.c_double, C.c_int64,
+                                        _i64p, _i64p, _i32p]
+        L.orc_batch.restype = C.c_int
+        L.orc_batch.argtypes = [C.c_int64, _i64p, _dp, _i32p, _dp, _u8p, C.POINTER(OrcDesc),
+                                C.POINTER(OrcArch), _dp, _i64p, _dp, _dp, _dp, _dp, _dp,
+                                _dp, _dp, C.c_double, _dp, _dp]
+        L.orc_sampled.restype = C.c_int
+        L.orc_sampled.argtypes = [C.c_int64, _dp, _i32p, _dp, _u8p, C.POINTER(OrcDesc),
+                                  C.POINTER(OrcArch), _dp, _i64p, C.c_int64, _i64p, C.c_int64,
+                                  _i32p, _i32p, _i64p, _dp, _dp, _dp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray], t):
+    if a is None:
+        return C.cast(None, t)
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(t)
+
+
+class _DescHolder:
+    """Keeps the parameter arrays alive while C holds pointers into them."""
+
+    def __init__(self, d):
+        self.rs_rad = np.ascontiguousarray(d.rs_rad, np.float64)
+        self.rs_ang = np.ascontiguousarray(d.rs_ang, np.float64)
+        self.theta_s = np.ascontiguousarray(d.theta_s, np.float64)
+        self.s = OrcDesc(int(d.n_species), float(d.rc), len(self.rs_rad), _ptr(self.rs_rad, _dp),
+                         float(d.eta_rad), len(self.rs_ang), _ptr(self.rs_ang, _dp),
+                         len(self.theta_s), _ptr(self.theta_s, _dp), float(d.eta_ang),
+                         float(d.zeta), float(d.eps_theta))
+
+
+def _arch(a) -> OrcArch:
+    s = OrcArch()
+    s.n_layers = a.n_layers
+    for k, w in enumerate(a.widths):
+        s.widths[k] = int(w)
+    for k, t in enumerate(a.acts):
+        s.act[k] = int(t)
+    return s
+
+
+def _archs(archs) -> C.Array:
+    arr = (OrcArch * len(archs))()
+    for k, a in enumerate(archs):
+        arr[k] = _arch(a)
+    return arr
+
+
+def _theta_off(archs) -> np.ndarray:
+    off = [0]
+    for a in archs:
+        off.append(off[-1] + a.n_params)
+    return np.asarray(off, np.int64)
+
+
+def descriptor_size(desc) -> int:
+    h = _DescHolder(desc)
+    return lib().orc_descriptor_size(C.byref(h.s))
+
+
+def center(desc, rv: np.ndarray, sp: np.ndarray, jacobian: bool = True):
+    """Descriptor G[D] of one centre with neighbour vectors rv[k,3] of species sp[k];
+    with ``jacobian`` also J[D,k,3] = dG/dr."""
+    h = _DescHolder(desc)
+    rv = np.ascontiguousarray(rv, np.float64).reshape(-1, 3)
+    sp = np.ascontiguousarray(sp, np.int32)
+    k = rv.shape[0]
+    D = lib().orc_descriptor_size(C.byref(h.s))
+    G = np.zeros(D)
+    J = np.zeros((D, k, 3)) if jacobian else None
+    lib().orc_center(C.byref(h.s), k, _ptr(rv, _dp), _ptr(sp, _i32p), _ptr(G, _dp), _ptr(J, _dp))
+    return (G, J) if jacobian else G
+
+
+def mlp(arch, theta_s: np.ndarray, x: np.ndarray, xdot: Optional[np.ndarray] = None,
+        alpha: float = 0.0, beta: float = 0.0, param_grad: bool = False):
+    """(E, g = dE/dx, dtheta) for one input vector through one species' network."""
+    a = _arch(arch)
+    th = np.ascontiguousarray(theta_s, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    xd = None if xdot is None else np.ascontiguousarray(xdot, np.float64)
+    E = np.zeros(1)
+    g = np.zeros(len(x))
+    dth = np.zeros(len(th)) if param_grad else None
+    lib().orc_mlp(C.byref(a), _ptr(th, _dp), _ptr(x, _dp), _ptr(E, _dp), _ptr(g, _dp),
+                  _ptr(xd, _dp), float(alpha), float(beta), _ptr(dth, _dp))
+    return float(E[0]), g, dth
+
+
+def neighbor_list(system, rc: float):
+    """Sorted (i, j, shift[.,3]) of every neighbour entry, global atom indices."""
+    s = system
+    off = np.ascontiguousarray(s.atom_off, np.int64)
+    pos = np.ascontiguousarray(s.pos, np.float64)
+    cell = np.ascontiguousarray(s.cell, np.float64)
+    pbc = np.ascontiguousarray(s.pbc, np.uint8)
+    L = lib()
+    cap = 0
+    while True:
+        ii = np.zeros(max(cap, 1), np.int64)
+        jj = np.zeros(max(cap, 1), np.int64)
+        sh = np.zeros((max(cap, 1), 3), np.int32)
+        n = L.orc_neighbor_list(s.n_cfg, _ptr(off, _i64p), _ptr(pos, _dp), _ptr(cell, _dp),
+                                _ptr(pbc, _u8p), float(rc), cap, _ptr(ii, _i64p), _ptr(jj, _i64p),
+                                _ptr(sh, _i32p))
+        if n <= cap:
+            return ii[:n], jj[:n], sh[:n]
+        cap = int(n)
+
+
+def batch(system, desc, archs, theta, want_G: bool = False, e_ref=None, f_ref=None,
+          w_force: float = 0.1, param_grad: bool = False):
+    """Whole-batch FP64 evaluation; returns a dict of numpy arrays (see orc_batch)."""
+    s = system
+    h = _DescHolder(desc)
+    D = lib().orc_descriptor_size(C.byref(h.s))
+    N, Cn = s.n_atoms, s.n_cfg
+    off = np.ascontiguousarray(s.atom_off, np.int64)
+    pos = np.ascontiguousarray(s.pos, np.float64)
+    spec = np.ascontiguousarray(s.species, np.int32)
+    cell = np.ascontiguousarray(s.cell, np.float64)
+    pbc = np.ascontiguousarray(s.pbc, np.uint8)
+    arr = _archs(archs)
+    th = np.ascontiguousarray(theta, np.float64)
+    toff = _theta_off(archs)
+    out = dict(E_atom=np.zeros(N), E_cfg=np.zeros(Cn), F=np.zeros((N, 3)), virial=np.zeros((Cn, 3, 3)))
+    G = np.zeros((N, D)) if want_G else None
+    er = None if e_ref is None else np.ascontiguousarray(e_ref, np.float64)
+    fr = None if f_ref is None else np.ascontiguousarray(f_ref, np.float64)
+    loss = np.zeros(1)
+    dth = np.zeros(len(th)) if (param_grad and er is not None) else None
+    lib().orc_batch(Cn, _ptr(off, _i64p), _ptr(pos, _dp), _ptr(spec, _i32p), _ptr(cell, _dp),
+                    _ptr(pbc, _u8p), C.byref(h.s), arr, _ptr(th, _dp), _ptr(toff, _i64p),
+                    _ptr(G, _dp), _ptr(out["E_atom"], _dp), _ptr(out["E_cfg"], _dp),
+                    _ptr(out["F"], _dp), _ptr(out["virial"], _dp), _ptr(er, _dp), _ptr(fr, _dp),
+                    float(w_force), _ptr(loss, _dp), _ptr(dth, _dp))
+    if want_G:
+        out["G"] = G
+    if er is not None:
+        out["loss"] = float(loss[0])
+    if dth is not None:
+        out["dtheta"] = dth
+    return out
+
+
+def workload_batch(wl, want_G=False, train=False):
+    return batch(wl.system, wl.desc, wl.archs, wl.theta, want_G=want_G,
+                 e_ref=wl.e_ref if train else None, f_ref=wl.f_ref if train else None,
+                 w_force=wl.w_force, param_grad=train)
+
+
+def sampled(system, cfg: int, desc, archs, theta, samples: Sequence[int], cap: int = 512):
+    """Per sampled atom (indices local to configuration ``cfg``): neighbour list, G, E_i,
+    force.  For configurations too large for :func:`batch`."""
+    s = system
+    a0, a1 = int(s.atom_off[cfg]), int(s.atom_off[cfg + 1])
+    n = a1 - a0
+    h = _DescHolder(desc)
+    D = lib().orc_descriptor_size(C.byref(h.s))
+    pos = np.ascontiguousarray(s.pos[a0:a1], np.float64)
+    spec = np.ascontiguousarray(s.species[a0:a1], np.int32)
+    cell = np.ascontiguousarray(s.cell[cfg], np.float64)
+    pbc = np.ascontiguousarray(s.pbc[cfg], np.uint8)
+    smp = np.ascontiguousarray(samples, np.int64)
+    ns = len(smp)
+    arr = _archs(archs)
+    th = np.ascontiguousarray(theta, np.float64)
+    toff = _theta_off(archs)
+    nbj = np.zeros((ns, cap), np.int32)
+    nbs = np.zeros((ns, cap, 3), np.int32)
+    nnb = np.zeros(ns, np.int64)
+    G = np.zeros((ns, D))
+    E = np.zeros(ns)
+    F = np.zeros((ns, 3))
+    lib().orc_sampled(n, _ptr(pos, _dp), _ptr(spec, _i32p), _ptr(cell, _dp), _ptr(pbc, _u8p),
+                      C.byref(h.s), arr, _ptr(th, _dp), _ptr(toff, _i64p), ns, _ptr(smp, _i64p),
+                      cap, _ptr(nbj, _i32p), _ptr(nbs, _i32p), _ptr(nnb, _i64p), _ptr(G, _dp),
+                      _ptr(E, _dp), _ptr(F, _dp))
+    if np.any(nnb > cap):
+        raise RuntimeError("neighbour capacity %d exceeded" % cap)
+    return dict(nnb=nnb, nb_j=nbj, nb_shift=nbs, G=G, E=E, F=F)
