@@ -1,0 +1,241 @@
+/*
+ * panna_gb300.h -- C ABI of the GB300 (sm_103a) energy / force / weight-gradient path of
+ * the PANNA 2.0 neural-network interatomic potential (arXiv 2305.11805).
+ *
+ * The method (Sec. II, II.A): every atom i gets a fixed-size descriptor G_i of its
+ * environment within a cutoff rc (species-resolved Behler-Parrinello radial terms and
+ * modified angular terms); a per-species multilayer perceptron (Eq. 1) maps G_i to an
+ * atomic energy E_i; the total energy is sum_i E_i and forces are -dE/dx.  Training
+ * matches energies and forces through a loss (Sec. II.A) whose gradient with respect to
+ * the network parameters needs a second derivative through the networks.
+ *
+ * Conventions shared by every call
+ *  - Memory: every pointer argument named "device" lives in CUDA device memory of the
+ *    current device and is owned by the caller; the library never frees it.  Arguments
+ *    marked "host" are host memory and are only read during the call.  The context owns
+ *    its workspace (device memory grown on demand, freed by panna_destroy).
+ *  - Streams: work is enqueued on the caller's stream `stream` (0 = legacy default).
+ *    Unless stated otherwise a call returns after its work has completed (it ends with a
+ *    stream synchronisation that also collects the device-side status word); see
+ *    panna_set_async for asynchronous operation.
+ *  - Errors: every call returns a panna_status and never throws across the ABI; the
+ *    message of the last failure on the calling thread is in panna_last_error().  Device
+ *    errors (neighbour-capacity overflow, invalid species, non-finite positions) land in
+ *    a status word on the device.  On PANNA_ERR_NEIGHBOR_OVERFLOW a synchronous call
+ *    has already grown its neighbour capacity and re-run once; it only fails if the
+ *    retry overflows too.
+ *  - Precision: positions and cells enter in FP64.  Descriptors, the descriptor adjoint
+ *    (forces) and the descriptor JVP run in FP32; the networks run in FP32 or in BF16 with
+ *    FP32 accumulation (mlp_precision); per-configuration energies, virials and the
+ *    loss are reduced in FP64.
+ *  - Units: Angstrom; energies in the units of the network output.
+ */
+#ifndef PANNA_GB300_H
+#define PANNA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* panna_stream_t;   /* same as cudaStream_t */
+
+typedef enum {
+    PANNA_OK = 0,
+    PANNA_ERR_INVALID_ARG = 1,        /* bad sizes, null pointers, inconsistent parameters */
+    PANNA_ERR_UNSUPPORTED = 2,        /* valid request outside what the kernels implement */
+    PANNA_ERR_NEIGHBOR_OVERFLOW = 3,  /* an atom had more neighbours than the capacity */
+    PANNA_ERR_TIMEOUT = 4,            /* a bounded device-side wait gave up */
+    PANNA_ERR_CUDA = 5,               /* a CUDA runtime call failed */
+    PANNA_ERR_NO_MEMORY = 6,          /* workspace allocation failed */
+    PANNA_ERR_BAD_INPUT = 7           /* species out of range or non-finite coordinates */
+} panna_status;
+
+/* Activation codes (Sec. II.A: Gaussian, ReLU, tanh; linear for the output). */
+enum { PANNA_ACT_LINEAR = 0, PANNA_ACT_GAUSSIAN = 1, PANNA_ACT_RELU = 2, PANNA_ACT_TANH = 3 };
+
+/* Network precision. */
+enum { PANNA_MLP_FP32 = 0, PANNA_MLP_BF16 = 1 };
+
+/*
+ * Descriptor parameters (host memory; copied by panna_create).
+ * Cutoff f_c(r) = (1 + cos(pi r / rc)) / 2 for r < rc.
+ * Radial block of neighbour species s, shell n (0 <= n < n_rad):
+ *     G[s*n_rad + n] = sum_j exp(-eta_rad (r_ij - rs_rad[n])^2) f_c(r_ij)
+ * Angular block of the unordered species pair {s_j, s_k} (blocks in upper-triangle
+ * row-major order (0,0),(0,1),..,(0,S-1),(1,1),..), entry m*n_ang_r + n:
+ *     G[...] = 2^(1-zeta) sum_{j<k} max(0, 1 + cos(theta_ijk - theta_s[m]))^zeta
+ *              exp(-eta_ang ((r_ij + r_ik)/2 - rs_ang[n])^2) f_c(r_ij) f_c(r_ik)
+ * with cos(theta - theta_m) = cos(theta) cos(theta_m) + sin(theta) sin(theta_m) and
+ * sin(theta) = sqrt(max(1 - cos^2(theta), 0) + eps_theta).
+ * Size D = S*n_rad + S(S+1)/2 * n_theta * n_ang_r (Sec. III.A, III.B sizes).
+ * The forms follow the standard BP / PANNA 1.0 mBP descriptors that Sec. II.A cites.
+ */
+typedef struct {
+    int32_t n_species;      /* S, 1..8 */
+    double rc;              /* cutoff (Angstrom), > 0 */
+    int32_t n_rad;          /* radial shells, 1..256 */
+    const double* rs_rad;   /* [n_rad] */
+    double eta_rad;         /* >= 0 */
+    int32_t n_ang_r;        /* angular radial shells, 1..64 */
+    const double* rs_ang;   /* [n_ang_r] */
+    int32_t n_theta;        /* angular sectors, 1..64 */
+    const double* theta_s;  /* [n_theta] */
+    double eta_ang;         /* >= 0 */
+    double zeta;            /* >= 1 */
+    double eps_theta;       /* >= 0 */
+} panna_desc_params;
+
+#define PANNA_MAX_LAYERS 8
+
+/*
+ * One species' network (Eq. 1): widths[0] = D, widths[n_layers] = 1, act[l] is the
+ * activation of layer l+1.  Parameters of a species, in order for l = 1..n_layers:
+ * W_l (row-major [widths[l]][widths[l-1]]) then b_l [widths[l]]; layer l computes
+ * z = W_l a + b_l.  The flat parameter vector of the model is the concatenation over
+ * species 0..S-1 (FP32).
+ */
+typedef struct {
+    int32_t n_layers;
+    int32_t widths[PANNA_MAX_LAYERS + 1];
+    int32_t act[PANNA_MAX_LAYERS];
+} panna_mlp_arch;
+
+/*
+ * A ragged batch of configurations (all device pointers, caller-owned):
+ *   atom_off [n_cfg+1] int64, atoms of configuration c are atom_off[c]..atom_off[c+1]-1,
+ *                     atom_off[0] = 0, atom_off[n_cfg] = n_atoms;
+ *   pos      [n_atoms*3] FP64 Cartesian positions (need not be folded into the cell);
+ *   species  [n_atoms] int32 in 0..S-1;
+ *   cell     [n_cfg*9] FP64, rows are the lattice vectors a, b, c;
+ *   pbc      [n_cfg*3] uint8 periodic flags per lattice direction.
+ * A configuration with no periodic direction ignores its cell.  Otherwise the cell must
+ * be non-singular.  n_cfg and n_atoms are host values.
+ */
+typedef struct {
+    int64_t n_cfg;
+    int64_t n_atoms;
+    const int64_t* atom_off;
+    const double* pos;
+    const int32_t* species;
+    const double* cell;
+    const uint8_t* pbc;
+} panna_system;
+
+typedef struct panna_ctx panna_ctx;
+
+/* Library version string. */
+const char* panna_version(void);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* panna_last_error(void);
+
+/* D for the given parameters (Sec. III.A / III.B sizes), or -1 if they are invalid. */
+int64_t panna_descriptor_size(const panna_desc_params* desc);
+
+/*
+ * Create a context bound to the current CUDA device.  `archs` (host) holds one network
+ * per species (n_archs must equal desc->n_species).  Fails with PANNA_ERR_UNSUPPORTED
+ * for layer widths the kernels do not implement (every width must be <= 1024, the input
+ * width must equal D).
+ */
+panna_status panna_create(const panna_desc_params* desc, int32_t n_archs,
+                          const panna_mlp_arch* archs, panna_ctx** out);
+
+/* Release the context and its workspace (no-op for NULL). */
+void panna_destroy(panna_ctx* ctx);
+
+/* Total number of network parameters over all species (length of theta / dtheta). */
+int64_t panna_param_count(const panna_ctx* ctx);
+
+/* Per-atom neighbour capacity used by the next call (grown automatically on overflow). */
+panna_status panna_set_neighbor_capacity(panna_ctx* ctx, int32_t cap);
+int32_t panna_neighbor_capacity(const panna_ctx* ctx);
+
+/*
+ * async = 0 (default): every compute call synchronises `stream` at its end, checks the
+ * device status word and retries once on neighbour overflow.  async = 1: calls only
+ * enqueue work (no synchronisation, no retry); call panna_check afterwards.  Workspace
+ * is sized on the first call for a given number of atoms, so a call with a new size is
+ * never graph-capturable; repeat calls with the same sizes allocate nothing.
+ */
+panna_status panna_set_async(panna_ctx* ctx, int32_t async);
+
+/* Synchronise `stream` and return (and clear) the device status word. */
+panna_status panna_check(panna_ctx* ctx, panna_stream_t stream);
+
+/*
+ * Neighbour list (Sec. I locality, cutoff rc): every entry (i, j, n) with
+ * 0 < |x_j + n.cell - x_i| < rc, j != i or n != 0, including periodic self-images and
+ * several images of one atom in cells narrower than 2 rc.  Output in CSR form (device):
+ *   nbr_off [n_atoms+1] int64, entries of atom i at nbr_off[i]..nbr_off[i+1]-1,
+ *   nbr_j   [cap_total] int64 (global atom index), nbr_shift [cap_total*3] int32 (n).
+ * Within an atom the entries are grouped by neighbour species (ascending), in a fixed
+ * deterministic order inside a group.  *n_total (host) receives the number of entries;
+ * if it exceeds cap_total nothing is written past cap_total and the call returns
+ * PANNA_ERR_INVALID_ARG.  Always synchronous.
+ */
+panna_status panna_neighbors(panna_ctx* ctx, const panna_system* sys, int64_t cap_total,
+                             int64_t* nbr_off, int64_t* nbr_j, int32_t* nbr_shift,
+                             int64_t* n_total, panna_stream_t stream);
+
+/* Descriptors G [n_atoms*D] FP32 (device, row i = atom i).  Sec. II.A. */
+panna_status panna_descriptors(panna_ctx* ctx, const panna_system* sys, float* G,
+                               panna_stream_t stream);
+
+/*
+ * Energies and forces (Sec. II): theta [P] FP32 device parameters (layout above).
+ *   E_cfg  [n_cfg] FP64 per-configuration energy (device, required)
+ *   E_atom [n_atoms] FP32 atomic energies (device, may be NULL)
+ *   F      [n_atoms*3] FP32 forces -dE/dx (device, required)
+ *   virial [n_cfg*9] FP64, W_ab = -sum over neighbour entries q_a r_b with
+ *          q = dE_i/dr_ij (device, may be NULL)
+ * mlp_precision: PANNA_MLP_FP32 or PANNA_MLP_BF16 (BF16 operands, FP32 accumulation).
+ */
+panna_status panna_energy_forces(panna_ctx* ctx, const panna_system* sys, const float* theta,
+                                 int32_t mlp_precision, double* E_cfg, float* E_atom, float* F,
+                                 double* virial, panna_stream_t stream);
+
+/*
+ * Vector-Jacobian product of (E_cfg, F) with respect to the parameters: given upstream
+ * gradients dE [n_cfg] FP64 and dF [n_atoms*3] FP32 (either may be NULL = zero), writes
+ *   dtheta [P] FP32 = sum_c dE_c dE_c/dtheta + sum_{m,a} dF_ma dF_ma/dtheta.
+ * The force part is the double backward through the networks: with u = dF,
+ * w_i = sum_e dG_i/dr_e (u_j(e) - u_i) (descriptor JVP) and g_i = dE_i/dG_i,
+ * dtheta += -d/dtheta sum_i g_i . w_i.  Descriptors are recomputed, never stored with
+ * their Jacobians (Sec. II.A, on-the-fly descriptors).  FP32 networks only.
+ */
+panna_status panna_param_vjp(panna_ctx* ctx, const panna_system* sys, const float* theta,
+                             const double* dE, const float* dF, float* dtheta,
+                             panna_stream_t stream);
+
+/*
+ * One training step's loss and parameter gradient (Sec. II.A: quadratic energy and force
+ * terms with a relative factor, energy per configuration, force per component):
+ *   L = (1/C) sum_c (E_c - E_ref_c)^2 + w_force/(3N) sum_{m,a} (F_ma - F_ref_ma)^2
+ * E_ref [n_cfg] FP64 and F_ref [n_atoms*3] FP32 device inputs; outputs (device):
+ *   loss [1] FP64, dtheta [P] FP32 = dL/dtheta, and optionally E_cfg [n_cfg] FP64 and
+ *   F [n_atoms*3] FP32 (may be NULL).  FP32 networks only.
+ */
+panna_status panna_loss_grad(panna_ctx* ctx, const panna_system* sys, const float* theta,
+                             const double* E_ref, const float* F_ref, double w_force,
+                             double* loss, float* dtheta, double* E_cfg, float* F,
+                             panna_stream_t stream);
+
+/*
+ * Number of kernels the last compute call launched (for launch accounting), and the
+ * device time of the named stage of the last call in milliseconds when profiling is on
+ * (panna_set_profiling(ctx, 1) records CUDA events around each stage on `stream`).
+ * Stages: "neighbors", "descriptor", "mlp", "adjoint", "forces", "jvp", "mlp_grad",
+ * "loss".  Returns -1 for an unknown stage or when profiling is off.
+ */
+int32_t panna_last_launch_count(const panna_ctx* ctx);
+panna_status panna_set_profiling(panna_ctx* ctx, int32_t on);
+float panna_stage_ms(const panna_ctx* ctx, const char* stage);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PANNA_GB300_H */

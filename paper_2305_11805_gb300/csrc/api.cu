@@ -1,0 +1,583 @@
+// C ABI of libpanna_gb300: context, workspace and the sequencing of the stages of the
+// energy / force / weight-gradient path.  Every step of the path runs in the kernels of
+// this library; there is no host or CPU fallback.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "common.cuh"
+#include "mlp.cuh"
+
+using namespace panna;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+static panna_status fail(panna_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(PANNA_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define ST(call)                                  \
+    do {                                          \
+        panna_status s_ = (call);                 \
+        if (s_ != PANNA_OK) return s_;            \
+    } while (0)
+
+// ------------------------------------------------------------------ workspace arena
+
+namespace {
+
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    bool sizing = true;
+    template <class T>
+    T* take(size_t n)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = sizing ? nullptr : reinterpret_cast<T*>(base + off);
+        off += (n ? n : 1) * sizeof(T);
+        return p;
+    }
+};
+
+const char* kStages[] = {"neighbors", "descriptor", "mlp", "adjoint", "forces", "jvp", "mlp_grad", "loss"};
+constexpr int kNumStages = 8;
+
+}  // namespace
+
+struct panna_ctx {
+    int device = 0;
+    DescDev d{};
+    MlpPlan plan{};
+    int32_t cap = 64;
+    int async = 0;
+    int profiling = 0;
+    int last_launches = 0;
+    Arena ws;
+    DevStatus* h_status = nullptr;   // pinned
+    cudaEvent_t ev[kNumStages + 1] = {};
+    float stage_ms[kNumStages] = {};
+    bool stage_seen[kNumStages] = {};
+};
+
+// ------------------------------------------------------------------ workspace layout
+
+namespace {
+
+struct Layout {
+    Work w;
+    MlpBuffers mb;
+    float* G = nullptr;
+    float* g = nullptr;
+    float* E_rows = nullptr;
+    float* vir_atom = nullptr;
+    double* cfg_part = nullptr;
+    float* F_int = nullptr;
+    double* E_cfg_int = nullptr;
+    // training
+    float* u = nullptr;
+    double* alpha_cfg = nullptr;
+    float* alpha_rows = nullptr;
+    float* wdot = nullptr;
+    double* loss_part = nullptr;
+};
+
+constexpr int kSplits = 16;
+
+void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, Layout& L)
+{
+    const int S = c->d.S, D = c->d.D, cap = c->cap;
+    const MlpPlan& p = c->plan;
+    Work& w = L.w;
+    w.N = N; w.C = C; w.cap = cap;
+    w.cap_cells = 2 * N + C + 1;
+    w.status = a.take<DevStatus>(1);
+    w.geom = a.take<CfgGeom>(C);
+    w.cell_count = a.take<int64_t>(w.cap_cells + 1);
+    w.cell_start = a.take<int64_t>(w.cap_cells + 1);
+    w.cell_fill = a.take<int32_t>(w.cap_cells);
+    w.cell_atoms = a.take<int32_t>(N);
+    w.atom_cell = a.take<int32_t>(N);
+    w.atom_cfg = a.take<int32_t>(N);
+    w.pos_hi = a.take<float4>(N);
+    w.pos_lo = a.take<float4>(N);
+    w.wrap = a.take<int32_t>(3 * N);
+    int64_t mx = w.cap_cells + 1 > N + 1 ? w.cap_cells + 1 : N + 1;
+    w.scan_tmp = a.take<int64_t>(scan_scratch_elems(mx));
+    w.nb_count = a.take<int32_t>(N);
+    w.nb_vec = a.take<float4>((size_t)N * cap);
+    w.nb_idx = a.take<int2>((size_t)N * cap);
+    w.row_of_atom = a.take<int32_t>(N);
+    w.atom_of_row = a.take<int32_t>(N);
+    w.seg_off = a.take<int32_t>(S + 1);
+    w.blk_counts = a.take<int32_t>(((N + 1023) / 1024 + 1) * S);
+    L.G = a.take<float>((size_t)N * D);
+    L.g = a.take<float>((size_t)N * D);
+    L.E_rows = a.take<float>(N);
+    L.vir_atom = a.take<float>(9 * (size_t)N);
+    L.cfg_part = a.take<double>((size_t)C * cfg_chunks(N, C) * 10);
+    L.F_int = a.take<float>(3 * (size_t)N);
+    L.E_cfg_int = a.take<double>(C);
+    MlpBuffers& b = L.mb;
+    b.G = L.G;
+    for (int l = 1; l <= p.L; ++l) {
+        b.Z[l] = a.take<float>((size_t)N * p.ld[l]);
+        b.A[l] = a.take<float>((size_t)N * p.ld[l]);
+    }
+    b.Ab = a.take<float>((size_t)N * p.max_hidden);
+    b.Ab2 = a.take<float>((size_t)N * p.max_hidden);
+    b.seg_off = w.seg_off;
+    b.tile_start = a.take<int32_t>(S + 1);
+    b.splits = kSplits;
+    if (train) {
+        for (int l = 1; l <= p.L; ++l) {
+            b.Zd[l] = a.take<float>((size_t)N * p.ld[l]);
+            b.Ad[l] = a.take<float>((size_t)N * p.ld[l]);
+        }
+        b.Adb = a.take<float>((size_t)N * p.max_hidden);
+        b.Zb = a.take<float>((size_t)N * p.max_hidden);
+        b.Zdb = a.take<float>((size_t)N * p.max_hidden);
+        b.part = a.take<float>((size_t)kSplits * p.P);
+        L.u = a.take<float>(3 * (size_t)N);
+        L.alpha_cfg = a.take<double>(C);
+        L.alpha_rows = a.take<float>(N);
+        L.wdot = a.take<float>((size_t)N * D);
+        L.loss_part = a.take<double>(kLossParts);
+    }
+}
+
+panna_status prepare(panna_ctx* c, const panna_system* sys, bool train, Layout& L, cudaStream_t s)
+{
+    const int64_t N = sys->n_atoms, C = sys->n_cfg;
+    Arena sz;
+    sz.sizing = true;
+    carve(c, sz, N, C, train, L);
+    if (sz.off > c->ws.cap) {
+        if (c->ws.base) {
+            CU(cudaStreamSynchronize(s));
+            CU(cudaFree(c->ws.base));
+            c->ws.base = nullptr;
+            c->ws.cap = 0;
+        }
+        size_t want = sz.off + sz.off / 8;
+        cudaError_t e = cudaMalloc((void**)&c->ws.base, want);
+        if (e != cudaSuccess) {
+            c->ws.base = nullptr;
+            return fail(PANNA_ERR_NO_MEMORY, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+        }
+        c->ws.cap = want;
+    }
+    Arena real = c->ws;
+    real.sizing = false;
+    real.off = 0;
+    carve(c, real, N, C, train, L);
+    L.w.sys = sys;
+    return PANNA_OK;
+}
+
+panna_status check_system(const panna_ctx* c, const panna_system* sys)
+{
+    if (!c || !sys) return fail(PANNA_ERR_INVALID_ARG, "null context or system");
+    if (sys->n_cfg < 1 || sys->n_atoms < 0) return fail(PANNA_ERR_INVALID_ARG, "n_cfg must be >= 1, n_atoms >= 0");
+    if (sys->n_atoms > ((int64_t)1 << 31) - 1) return fail(PANNA_ERR_UNSUPPORTED, "more than 2^31-1 atoms");
+    if (!sys->atom_off || !sys->cell || !sys->pbc || (sys->n_atoms > 0 && (!sys->pos || !sys->species)))
+        return fail(PANNA_ERR_INVALID_ARG, "null system array");
+    return PANNA_OK;
+}
+
+void stage_mark(panna_ctx* c, int k, cudaStream_t s)
+{
+    if (c->profiling) {
+        cudaEventRecord(c->ev[k], s);
+        c->stage_seen[k] = true;
+    }
+}
+
+// Reads the status word (synchronising); returns it and the overflow requirement.
+panna_status collect(panna_ctx* c, const Layout& L, cudaStream_t s, int* need)
+{
+    CU(cudaMemcpyAsync(c->h_status, L.w.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    *need = c->h_status->need_cap;
+    if (c->h_status->code == 0) return PANNA_OK;
+    if (c->h_status->code == PANNA_ERR_NEIGHBOR_OVERFLOW)
+        return fail(PANNA_ERR_NEIGHBOR_OVERFLOW, "atom %d has %d neighbours, capacity %d", c->h_status->bad_index,
+                    c->h_status->need_cap, c->cap);
+    if (c->h_status->code == PANNA_ERR_BAD_INPUT)
+        return fail(PANNA_ERR_BAD_INPUT, "invalid input at index %d (species out of range, non-finite or coincident"
+                    " positions, or singular cell)", c->h_status->bad_index);
+    return fail((panna_status)c->h_status->code, "device error %d at index %d", c->h_status->code,
+                c->h_status->bad_index);
+}
+
+void finish_profile(panna_ctx* c)
+{
+    if (!c->profiling) return;
+    cudaEventSynchronize(c->ev[kNumStages]);
+    int prev = -1;
+    for (int k = 0; k <= kNumStages; ++k) {
+        if (k < kNumStages && !c->stage_seen[k]) continue;
+        if (prev >= 0) cudaEventElapsedTime(&c->stage_ms[prev], c->ev[prev], c->ev[k]);
+        prev = k;
+    }
+}
+
+// The core sequence; flags select what is computed.
+struct Request {
+    const float* theta = nullptr;
+    int prec = PANNA_MLP_FP32;
+    double* E_cfg = nullptr;
+    float* E_atom = nullptr;
+    float* F = nullptr;
+    double* virial = nullptr;
+    float* G_out = nullptr;     // descriptors only
+    bool forces = false;
+    bool energy = false;
+    // parameter gradient
+    bool train = false;         // loss from E_ref/F_ref
+    bool vjp = false;           // upstream dE/dF given
+    const double* E_ref = nullptr;
+    const float* F_ref = nullptr;
+    double w_force = 0.0;
+    double* loss = nullptr;
+    const double* dE = nullptr;
+    const float* dF = nullptr;
+    float* dtheta = nullptr;
+};
+
+panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, Layout& L, cudaStream_t s)
+{
+    int& nl = c->last_launches;
+    const int64_t N = sys->n_atoms;
+    const bool grad = rq.train || rq.vjp;
+    for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
+    CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
+    stage_mark(c, 0, s);
+    CU(build_neighbors(L.w, c->d, s, &nl));
+    if (rq.G_out) {
+        stage_mark(c, 1, s);
+        CU(launch_descriptor(L.w, c->d, rq.G_out, nullptr, s, &nl));
+        if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
+        return PANNA_OK;
+    }
+    CU(species_order(L.w, c->d.S, s, &nl));
+    CU(mlp_tiles(c->plan, L.w.seg_off, L.mb.tile_start, s, &nl));
+    stage_mark(c, 1, s);
+    CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, s, &nl));
+    stage_mark(c, 2, s);
+    CU(mlp_forward(c->plan, L.mb, rq.theta, N, s, &nl));
+    CU(mlp_energy_rows(c->plan, L.mb, N, L.E_rows, s, &nl));
+    float* F = rq.F ? rq.F : L.F_int;
+    double* E_cfg = rq.E_cfg ? rq.E_cfg : L.E_cfg_int;
+    const bool need_forces = rq.forces || rq.train;
+    if (need_forces) {
+        CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl));
+        stage_mark(c, 3, s);
+        CU(cudaMemsetAsync(F, 0, sizeof(float) * 3 * N, s));
+        CU(launch_adjoint(L.w, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, s, &nl));
+    }
+    stage_mark(c, 4, s);
+    CU(launch_cfg_reduce(L.w, L.E_rows, (rq.virial && need_forces) ? L.vir_atom : nullptr, E_cfg, rq.virial,
+                         rq.E_atom, L.cfg_part, s, &nl));
+    if (grad) {
+        const float* u = nullptr;
+        const double* alpha = nullptr;
+        if (rq.train) {
+            stage_mark(c, 7, s);
+            CU(launch_loss(L.w, E_cfg, rq.E_ref, F, rq.F_ref, rq.w_force, rq.loss, L.alpha_cfg, L.u, L.loss_part, s, &nl));
+            u = L.u;
+            alpha = L.alpha_cfg;
+        } else {
+            u = rq.dF;
+            alpha = rq.dE;
+        }
+        CU(launch_row_scale(L.w, alpha, L.alpha_rows, s, &nl));
+        stage_mark(c, 5, s);
+        if (u) {
+            CU(launch_jvp(L.w, c->d, u, L.wdot, s, &nl));
+        } else {
+            CU(cudaMemsetAsync(L.wdot, 0, sizeof(float) * (size_t)N * c->d.D, s));
+        }
+        stage_mark(c, 6, s);
+        CU(mlp_param_grad(c->plan, L.mb, rq.theta, N, L.wdot, L.alpha_rows, rq.dtheta, s, &nl));
+    }
+    if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
+    return PANNA_OK;
+}
+
+panna_status run(panna_ctx* c, const panna_system* sys, const Request& rq, cudaStream_t s)
+{
+    ST(check_system(c, sys));
+    CU(cudaSetDevice(c->device));
+    const bool train = rq.train || rq.vjp;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        Layout L;
+        ST(prepare(c, sys, train, L, s));
+        c->last_launches = 0;
+        ST(run_once(c, sys, rq, L, s));
+        CU(cudaGetLastError());
+        if (c->async) return PANNA_OK;
+        int need = 0;
+        panna_status st = collect(c, L, s, &need);
+        finish_profile(c);
+        if (st == PANNA_ERR_NEIGHBOR_OVERFLOW && attempt == 0) {
+            c->cap = need + need / 4 + 8;
+            continue;
+        }
+        return st;
+    }
+    return PANNA_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ public API
+
+extern "C" {
+
+const char* panna_version(void) { return "panna_gb300 0.1 (sm_103a)"; }
+
+const char* panna_last_error(void) { return g_last_error.c_str(); }
+
+static int64_t desc_size(const panna_desc_params* p)
+{
+    if (!p) return -1;
+    if (p->n_species < 1 || p->n_species > kMaxSpecies) return -1;
+    if (p->n_rad < 1 || p->n_ang_r < 1 || p->n_theta < 1) return -1;
+    const int64_t S = p->n_species;
+    return S * p->n_rad + S * (S + 1) / 2 * p->n_theta * p->n_ang_r;
+}
+
+int64_t panna_descriptor_size(const panna_desc_params* p) { return desc_size(p); }
+
+panna_status panna_create(const panna_desc_params* p, int32_t n_archs, const panna_mlp_arch* archs, panna_ctx** out)
+{
+    if (!out) return fail(PANNA_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    const int64_t D = desc_size(p);
+    if (D < 0) return fail(PANNA_ERR_INVALID_ARG, "invalid descriptor sizes or species count (1..%d)", kMaxSpecies);
+    if (p->n_rad > kMaxRad || p->n_ang_r > kMaxAngR || p->n_theta > kMaxTheta)
+        return fail(PANNA_ERR_UNSUPPORTED, "grid larger than %d radial / %d angular-radial / %d theta", kMaxRad,
+                    kMaxAngR, kMaxTheta);
+    if (!(p->rc > 0.0) || !(p->eta_rad >= 0.0) || !(p->eta_ang >= 0.0) || !(p->zeta >= 1.0) || !(p->eps_theta >= 0.0))
+        return fail(PANNA_ERR_INVALID_ARG, "rc > 0, eta >= 0, zeta >= 1, eps_theta >= 0 required");
+    if (!p->rs_rad || !p->rs_ang || !p->theta_s) return fail(PANNA_ERR_INVALID_ARG, "null parameter grid");
+    if (n_archs != p->n_species || !archs) return fail(PANNA_ERR_INVALID_ARG, "one network per species required");
+    panna_ctx* c = new panna_ctx();
+    cudaGetDevice(&c->device);
+    DescDev& d = c->d;
+    d.S = p->n_species; d.n_rad = p->n_rad; d.n_ang_r = p->n_ang_r; d.n_theta = p->n_theta;
+    d.D = (int)D; d.n_blocks = d.S * (d.S + 1) / 2; d.rad_cols = d.S * d.n_rad;
+    d.rc = (float)p->rc; d.rc2 = d.rc * d.rc; d.rc_d = p->rc;
+    d.eta_rad = (float)p->eta_rad; d.eta_ang = (float)p->eta_ang; d.zeta = (float)p->zeta;
+    d.eps_theta = (float)p->eps_theta;
+    d.pi_rc = (float)(M_PI / p->rc);
+    d.zeta_int = (p->zeta == floor(p->zeta) && p->zeta <= 4096.0) ? (int)p->zeta : 0;
+    for (int k = 0; k < p->n_rad; ++k) c->d.rs_rad[k] = (float)p->rs_rad[k];
+    for (int k = 0; k < p->n_ang_r; ++k) c->d.rs_ang[k] = (float)p->rs_ang[k];
+    for (int k = 0; k < p->n_theta; ++k) {
+        c->d.half_cos_t[k] = (float)(0.5 * cos(p->theta_s[k]));
+        c->d.half_sin_t[k] = (float)(0.5 * sin(p->theta_s[k]));
+    }
+    MlpPlan& pl = c->plan;
+    pl.S = d.S;
+    pl.L = archs[0].n_layers;
+    int64_t off = 0;
+    for (int s = 0; s < d.S; ++s) {
+        const panna_mlp_arch& a = archs[s];
+        if (a.n_layers != pl.L || a.n_layers < 1 || a.n_layers > kMaxLayers) {
+            delete c;
+            return fail(PANNA_ERR_UNSUPPORTED, "every species needs the same number of layers (1..%d)", kMaxLayers);
+        }
+        if (a.widths[0] != D || a.widths[a.n_layers] != 1) {
+            delete c;
+            return fail(PANNA_ERR_INVALID_ARG, "species %d: input width must be D=%lld and output width 1", s,
+                        (long long)D);
+        }
+        for (int l = 0; l < a.n_layers; ++l) {
+            if (a.widths[l + 1] < 1 || a.widths[l + 1] > 1024 || a.act[l] < 0 || a.act[l] > 3) {
+                delete c;
+                return fail(PANNA_ERR_UNSUPPORTED, "species %d layer %d: width 1..1024 and activation 0..3", s, l + 1);
+            }
+            pl.widths[s][l] = a.widths[l];
+            pl.acts[s][l] = a.act[l];
+            pl.w_off[s][l] = off;
+            off += (int64_t)a.widths[l + 1] * a.widths[l];
+            pl.b_off[s][l] = off;
+            off += a.widths[l + 1];
+        }
+        pl.widths[s][a.n_layers] = 1;
+    }
+    pl.P = off;
+    pl.max_hidden = 1;
+    for (int l = 0; l <= pl.L; ++l) {
+        int m = 0;
+        for (int s = 0; s < d.S; ++s) m = pl.widths[s][l] > m ? pl.widths[s][l] : m;
+        pl.ld[l] = m;
+        if (l >= 1 && m > pl.max_hidden) pl.max_hidden = m;
+    }
+    if (cudaMallocHost((void**)&c->h_status, sizeof(DevStatus)) != cudaSuccess) {
+        delete c;
+        return fail(PANNA_ERR_CUDA, "pinned status allocation failed");
+    }
+    for (int k = 0; k <= kNumStages; ++k) cudaEventCreate(&c->ev[k]);
+    *out = c;
+    return PANNA_OK;
+}
+
+void panna_destroy(panna_ctx* c)
+{
+    if (!c) return;
+    if (c->ws.base) cudaFree(c->ws.base);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    for (int k = 0; k <= kNumStages; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    delete c;
+}
+
+int64_t panna_param_count(const panna_ctx* c) { return c ? c->plan.P : -1; }
+
+panna_status panna_set_neighbor_capacity(panna_ctx* c, int32_t cap)
+{
+    if (!c || cap < 1 || cap > 4096) return fail(PANNA_ERR_INVALID_ARG, "capacity must be 1..4096");
+    c->cap = cap;
+    return PANNA_OK;
+}
+
+int32_t panna_neighbor_capacity(const panna_ctx* c) { return c ? c->cap : -1; }
+
+panna_status panna_set_async(panna_ctx* c, int32_t async)
+{
+    if (!c) return fail(PANNA_ERR_INVALID_ARG, "null context");
+    c->async = async ? 1 : 0;
+    return PANNA_OK;
+}
+
+panna_status panna_check(panna_ctx* c, panna_stream_t stream)
+{
+    if (!c) return fail(PANNA_ERR_INVALID_ARG, "null context");
+    if (!c->ws.base) return PANNA_OK;
+    CU(cudaMemcpyAsync(c->h_status, c->ws.base, sizeof(DevStatus), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    DevStatus st = *c->h_status;
+    CU(cudaMemsetAsync(c->ws.base, 0, sizeof(DevStatus), (cudaStream_t)stream));
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    if (st.code == PANNA_ERR_NEIGHBOR_OVERFLOW) {
+        c->cap = st.need_cap + st.need_cap / 4 + 8;
+        return fail(PANNA_ERR_NEIGHBOR_OVERFLOW, "neighbour capacity exceeded (needed %d); capacity raised to %d",
+                    st.need_cap, c->cap);
+    }
+    if (st.code) return fail((panna_status)st.code, "device error %d at index %d", st.code, st.bad_index);
+    return PANNA_OK;
+}
+
+panna_status panna_neighbors(panna_ctx* c, const panna_system* sys, int64_t cap_total, int64_t* nbr_off,
+                             int64_t* nbr_j, int32_t* nbr_shift, int64_t* n_total, panna_stream_t stream)
+{
+    ST(check_system(c, sys));
+    if (!nbr_off || !n_total) return fail(PANNA_ERR_INVALID_ARG, "null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(c->device));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        Layout L;
+        ST(prepare(c, sys, false, L, s));
+        c->last_launches = 0;
+        CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
+        CU(build_neighbors(L.w, c->d, s, &c->last_launches));
+        int need = 0;
+        panna_status st = collect(c, L, s, &need);
+        if (st == PANNA_ERR_NEIGHBOR_OVERFLOW && attempt == 0) {
+            c->cap = need + need / 4 + 8;
+            continue;
+        }
+        if (st != PANNA_OK) return st;
+        CU(export_neighbors(L.w, nbr_off, nbr_j, nbr_shift, cap_total, s, &c->last_launches));
+        CU(cudaMemcpyAsync(n_total, nbr_off + sys->n_atoms, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (*n_total > cap_total)
+            return fail(PANNA_ERR_INVALID_ARG, "%lld entries, output holds %lld", (long long)*n_total,
+                        (long long)cap_total);
+        return PANNA_OK;
+    }
+    return PANNA_OK;
+}
+
+panna_status panna_descriptors(panna_ctx* c, const panna_system* sys, float* G, panna_stream_t stream)
+{
+    if (!G) return fail(PANNA_ERR_INVALID_ARG, "null G");
+    Request rq;
+    rq.G_out = G;
+    return run(c, sys, rq, (cudaStream_t)stream);
+}
+
+panna_status panna_energy_forces(panna_ctx* c, const panna_system* sys, const float* theta, int32_t prec,
+                                 double* E_cfg, float* E_atom, float* F, double* virial, panna_stream_t stream)
+{
+    if (!theta || !E_cfg || !F) return fail(PANNA_ERR_INVALID_ARG, "theta, E_cfg and F are required");
+    if (prec != PANNA_MLP_FP32 && prec != PANNA_MLP_BF16) return fail(PANNA_ERR_INVALID_ARG, "bad precision");
+    if (prec == PANNA_MLP_BF16) return fail(PANNA_ERR_UNSUPPORTED, "BF16 networks are not available yet");
+    Request rq;
+    rq.theta = theta; rq.prec = prec; rq.E_cfg = E_cfg; rq.E_atom = E_atom; rq.F = F; rq.virial = virial;
+    rq.forces = true; rq.energy = true;
+    return run(c, sys, rq, (cudaStream_t)stream);
+}
+
+panna_status panna_param_vjp(panna_ctx* c, const panna_system* sys, const float* theta, const double* dE,
+                             const float* dF, float* dtheta, panna_stream_t stream)
+{
+    if (!theta || !dtheta) return fail(PANNA_ERR_INVALID_ARG, "theta and dtheta are required");
+    Request rq;
+    rq.theta = theta; rq.vjp = true; rq.dE = dE; rq.dF = dF; rq.dtheta = dtheta; rq.energy = true;
+    return run(c, sys, rq, (cudaStream_t)stream);
+}
+
+panna_status panna_loss_grad(panna_ctx* c, const panna_system* sys, const float* theta, const double* E_ref,
+                             const float* F_ref, double w_force, double* loss, float* dtheta, double* E_cfg, float* F,
+                             panna_stream_t stream)
+{
+    if (!theta || !E_ref || !F_ref || !loss || !dtheta)
+        return fail(PANNA_ERR_INVALID_ARG, "theta, E_ref, F_ref, loss and dtheta are required");
+    Request rq;
+    rq.theta = theta; rq.train = true; rq.E_ref = E_ref; rq.F_ref = F_ref; rq.w_force = w_force; rq.loss = loss;
+    rq.dtheta = dtheta; rq.E_cfg = E_cfg; rq.F = F; rq.forces = true; rq.energy = true;
+    return run(c, sys, rq, (cudaStream_t)stream);
+}
+
+int32_t panna_last_launch_count(const panna_ctx* c) { return c ? c->last_launches : -1; }
+
+panna_status panna_set_profiling(panna_ctx* c, int32_t on)
+{
+    if (!c) return fail(PANNA_ERR_INVALID_ARG, "null context");
+    c->profiling = on ? 1 : 0;
+    return PANNA_OK;
+}
+
+float panna_stage_ms(const panna_ctx* c, const char* stage)
+{
+    if (!c || !stage || !c->profiling) return -1.f;
+    for (int k = 0; k < kNumStages; ++k)
+        if (strcmp(stage, kStages[k]) == 0) return c->stage_seen[k] ? c->stage_ms[k] : -1.f;
+    return -1.f;
+}
+
+}  // extern "C"

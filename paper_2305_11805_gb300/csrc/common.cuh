@@ -1,0 +1,121 @@
+// Internal declarations shared by the CUDA translation units of libpanna_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/panna_gb300.h"
+
+namespace panna {
+
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxLayers = PANNA_MAX_LAYERS;
+
+// Device status word: first error code wins; need_cap records the largest neighbour
+// count seen when an atom overflowed its capacity.
+struct DevStatus {
+    int32_t code;
+    int32_t need_cap;
+    int32_t bad_index;
+    int32_t pad;
+};
+
+__device__ __forceinline__ void set_status(DevStatus* st, int32_t code, int32_t idx)
+{
+    if (atomicCAS(&st->code, 0, code) == 0) st->bad_index = idx;
+}
+
+// Descriptor parameters as the kernels read them (FP32 copies plus FP64 cutoff).  The
+// struct is passed by value, so the grids sit in the kernel-parameter constant bank.
+constexpr int kMaxRad = 256;
+constexpr int kMaxAngR = 64;
+constexpr int kMaxTheta = 64;
+struct DescDev {
+    int32_t S, n_rad, n_ang_r, n_theta, D, n_blocks, rad_cols;
+    int32_t zeta_int;      // zeta when it is an integer in [1, 4096], else 0
+    float rc, rc2, eta_rad, eta_ang, zeta, eps_theta;
+    float pi_rc;           // pi / rc
+    double rc_d;
+    float rs_rad[kMaxRad];
+    float rs_ang[kMaxAngR];
+    float half_cos_t[kMaxTheta];   // cos(theta_m) / 2
+    float half_sin_t[kMaxTheta];   // sin(theta_m) / 2
+};
+
+// Geometry of one configuration as binned on the device.
+struct CfgGeom {
+    double cell[9];     // rows a, b, c (identity frame for fully non-periodic configs)
+    double cinv[9];     // fractional (row) = x (row) * cinv
+    double lo[3];       // fractional origin of the grid
+    double inv_w[3];    // 1 / fractional width of a grid cell
+    int32_t n[3];       // grid cells per axis
+    int32_t K[3];       // cell-offset window per axis
+    int32_t per[3];     // periodic flags
+    int32_t ncells;
+    int64_t cell_base;  // global id of the first cell
+    float sh_hi[27][3]; // image shift t.cell for t in [-1,1]^3 as hi + lo floats
+    float sh_lo[27][3];
+};
+
+// Neighbour slot index packing: (t0+128) | (t1+128) << 8 | (t2+128) << 16 | species << 24
+__host__ __device__ __forceinline__ int32_t pack_meta(int t0, int t1, int t2, int sp)
+{
+    return (t0 + 128) | ((t1 + 128) << 8) | ((t2 + 128) << 16) | (sp << 24);
+}
+__host__ __device__ __forceinline__ int meta_species(int32_t m) { return (m >> 24) & 0xff; }
+__host__ __device__ __forceinline__ int meta_t(int32_t m, int a) { return ((m >> (8 * a)) & 0xff) - 128; }
+
+// Workspace pointers for one call (all device memory owned by the context).
+struct Work {
+    int64_t N, C, cap_cells;
+    int32_t cap;                 // neighbour slots per atom
+    const panna_system* sys;
+    DevStatus* status;
+    // binning
+    CfgGeom* geom;               // [C]
+    int64_t* cell_count;         // [cap_cells+1]
+    int64_t* cell_start;         // [cap_cells+1]
+    int32_t* cell_fill;          // [cap_cells]
+    int32_t* cell_atoms;         // [N]
+    int32_t* atom_cell;          // [N] local cell id within the config
+    int32_t* atom_cfg;           // [N]
+    float4* pos_hi;              // [N] folded position, hi part
+    float4* pos_lo;              // [N] lo part
+    int32_t* wrap;               // [N*3] integer lattice offset added by folding
+    int64_t* scan_tmp;           // scan scratch
+    // neighbours
+    int32_t* nb_count;           // [N]
+    float4* nb_vec;              // [N*cap] (dx, dy, dz, r)
+    int2* nb_idx;                // [N*cap] (j, meta)
+    // species order
+    int32_t* row_of_atom;        // [N]
+    int32_t* atom_of_row;        // [N]
+    int32_t* seg_off;            // [S+1] rows of species s: seg_off[s]..seg_off[s+1]-1
+    int32_t* blk_counts;         // species sort scratch
+};
+
+// launch helpers implemented in the .cu files
+int64_t scan_scratch_elems(int64_t n);
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s, int* launches);
+cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* launches);
+cudaError_t species_order(Work& w, int S, cudaStream_t s, int* launches);
+cudaError_t export_neighbors(const Work& w, int64_t* off, int64_t* nbr_j, int32_t* shift, int64_t cap_total, cudaStream_t s, int* launches);
+
+// descriptor family (descriptor.cu); row_map == nullptr writes row i for atom i
+cudaError_t launch_descriptor(const Work& w, const DescDev& d, float* G_rows, const int32_t* row_map, cudaStream_t s,
+                              int* launches);
+cudaError_t launch_adjoint(const Work& w, const DescDev& d, const float* g_rows, float* F, float* vir_atom,
+                           cudaStream_t s, int* launches);
+cudaError_t launch_jvp(const Work& w, const DescDev& d, const float* u, float* wdot_rows, cudaStream_t s, int* launches);
+
+// reductions (reduce.cu)
+int cfg_chunks(int64_t N, int64_t C);
+cudaError_t launch_cfg_reduce(const Work& w, const float* E_rows, const float* vir_atom, double* E_cfg, double* virial,
+                              float* E_atom, double* part, cudaStream_t s, int* launches);
+constexpr int kLossParts = 2 * 120;
+cudaError_t launch_loss(const Work& w, const double* E_cfg, const double* E_ref, const float* F, const float* F_ref,
+                        double w_force, double* loss, double* alpha_cfg, float* u, double* part, cudaStream_t s,
+                        int* launches);
+cudaError_t launch_row_scale(const Work& w, const double* alpha_cfg, float* alpha_rows, cudaStream_t s, int* launches);
+
+}  // namespace panna

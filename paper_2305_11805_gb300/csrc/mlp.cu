@@ -1,0 +1,397 @@
+// Per-species multilayer perceptrons (Eq. 1) on species-sorted atom rows, FP32 CUDA-core
+// path: grouped GEMMs with fused bias / activation epilogues, the input gradient
+// dE/dG, the forward tangent along a descriptor direction, and the weight gradient of
+// the reverse pass over forward + tangent (the double backward of the force loss).
+//
+// Rows of species s are seg_off[s]..seg_off[s+1]-1 (device); the tile table maps a
+// CTA to (species, 64-row tile) without the host knowing the species counts, so one
+// launch covers all species and the launch shape depends only on N and S.
+#include "mlp.cuh"
+
+namespace panna {
+
+__device__ __forceinline__ float act_f(int t, float z)
+{
+    switch (t) {
+    case PANNA_ACT_GAUSSIAN: return __expf(-z * z);
+    case PANNA_ACT_RELU: return z > 0.f ? z : 0.f;
+    case PANNA_ACT_TANH: return tanhf(z);
+    default: return z;
+    }
+}
+__device__ __forceinline__ float act_d1(int t, float z)
+{
+    switch (t) {
+    case PANNA_ACT_GAUSSIAN: return -2.f * z * __expf(-z * z);
+    case PANNA_ACT_RELU: return z > 0.f ? 1.f : 0.f;
+    case PANNA_ACT_TANH: { float h = tanhf(z); return 1.f - h * h; }
+    default: return 1.f;
+    }
+}
+__device__ __forceinline__ float act_d2(int t, float z)
+{
+    switch (t) {
+    case PANNA_ACT_GAUSSIAN: return (4.f * z * z - 2.f) * __expf(-z * z);
+    case PANNA_ACT_TANH: { float h = tanhf(z); return -2.f * h * (1.f - h * h); }
+    default: return 0.f;
+    }
+}
+
+__global__ void k_tiles(int S, const int32_t* __restrict__ seg_off, int32_t* __restrict__ tile_start)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int t = 0;
+        for (int s = 0; s < S; ++s) {
+            tile_start[s] = t;
+            t += (seg_off[s + 1] - seg_off[s] + kBM - 1) / kBM;
+        }
+        tile_start[S] = t;
+    }
+}
+
+__device__ __forceinline__ bool tile_species(int S, const int32_t* tile_start, int tile, int& s)
+{
+    if (tile >= tile_start[S]) return false;
+    s = 0;
+    while (tile >= tile_start[s + 1]) ++s;
+    return true;
+}
+
+// C[rows, N] = op(A)[rows, K] * op(B)[K, N]
+//   B_TRANS (forward / tangent): op(B)[k][n] = W[n*K + k] (W is [N, K])
+//   else     (input gradient):   op(B)[k][n] = W[k*N + n] (W is [K, N])
+// PRO_DACT: A[r][k] is multiplied by act'(Zp[r][k]) on load (layer activation la.pact).
+// EPI_FWD:  C = Z = acc + b, C2 = act(Z);  EPI_TAN: C = acc, C2 = act'(Ze) * acc.
+template <bool B_TRANS, int PRO, int EPI>
+__global__ void __launch_bounds__(256)
+k_gemm(LayerArgs la, const float* __restrict__ theta, const int32_t* __restrict__ seg_off,
+       const int32_t* __restrict__ tile_start, const float* __restrict__ A, int lda,
+       const float* __restrict__ Zp, int ldp, float* __restrict__ C, int ldc, float* __restrict__ C2,
+       const float* __restrict__ Ze, int lde)
+{
+    __shared__ float As[kBK][kBM + 4];
+    __shared__ float Bs[kBK][kBN + 4];
+    int s;
+    if (!tile_species(la.S, tile_start, blockIdx.x, s)) return;
+    const int K = la.K[s], N = la.N[s];
+    const int n0 = blockIdx.y * kBN;
+    if (n0 >= N) return;
+    const int r0 = seg_off[s] + (blockIdx.x - tile_start[s]) * kBM;
+    const int rend = seg_off[s + 1];
+    const float* W = theta + la.w_off[s];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += kBK) {
+        {   // A tile: 64 rows x 16 k
+            const int m = tid >> 2, kq = (tid & 3) * 4;
+            const int r = r0 + m;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = k0 + kq + j;
+                float v = 0.f;
+                if (r < rend && k < K) {
+                    v = A[(size_t)r * lda + k];
+                    if (PRO == PRO_DACT) v *= act_d1(la.pact[s], Zp[(size_t)r * ldp + k]);
+                }
+                As[kq + j][m] = v;
+            }
+        }
+        if (B_TRANS) {   // W [N, K]: 64 n x 16 k
+            const int nn = tid >> 2, kq = (tid & 3) * 4;
+            const int n = n0 + nn;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = k0 + kq + j;
+                Bs[kq + j][nn] = (n < N && k < K) ? W[(size_t)n * K + k] : 0.f;
+            }
+        } else {         // W [K, N]: 16 k x 64 n
+            const int kk = tid >> 4, nq = (tid & 15) * 4;
+            const int k = k0 + kk;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = n0 + nq + j;
+                Bs[kk][nq + j] = (n < N && k < K) ? W[(size_t)k * N + n] : 0.f;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { a[q] = As[kk][ty * 4 + q]; b[q] = Bs[kk][tx * 4 + q]; }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+    const float* bias = theta + la.b_off[s];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int r = r0 + ty * 4 + p;
+        if (r >= rend) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int n = n0 + tx * 4 + q;
+            if (n >= N) continue;
+            float v = acc[p][q];
+            if (EPI == EPI_FWD) {
+                v += bias[n];
+                C[(size_t)r * ldc + n] = v;
+                C2[(size_t)r * ldc + n] = act_f(la.act[s], v);
+            } else if (EPI == EPI_TAN) {
+                C[(size_t)r * ldc + n] = v;
+                C2[(size_t)r * ldc + n] = act_d1(la.act[s], Ze[(size_t)r * lde + n]) * v;
+            } else {
+                C[(size_t)r * ldc + n] = v;
+            }
+        }
+    }
+}
+
+// part[split][w_off + m*K + n] = sum over rows of Zb[r][m] * A[r][n] (+ Zdb[r][m] * Ad[r][n]);
+// column n == K is the bias (A = 1, Ad = 0) -> part[split][b_off + m].
+// la.K = input width (n), la.N = output width (m).
+__global__ void __launch_bounds__(256)
+k_wgrad(LayerArgs la, const int32_t* __restrict__ seg_off, int splits,
+        const float* __restrict__ Zb, const float* __restrict__ A, int ldz, int lda,
+        const float* __restrict__ Zdb, const float* __restrict__ Ad, float* __restrict__ part, int64_t P)
+{
+    __shared__ float As[kBK][kBM + 4];
+    __shared__ float Bs[kBK][kBN + 4];
+    const int s = blockIdx.z / splits, split = blockIdx.z % splits;
+    const int K = la.K[s], N = la.N[s];
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+    if (m0 >= N || n0 >= K + 1) return;
+    const int rs = seg_off[s], re = seg_off[s + 1];
+    const int cnt = re - rs;
+    const int per = (cnt + splits - 1) / splits;
+    const int r0 = rs + split * per;
+    const int r1 = min(re, r0 + per);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    const int npass = Zdb ? 2 : 1;
+    for (int pass = 0; pass < npass; ++pass) {
+        const float* Zs = pass ? Zdb : Zb;
+        const float* As_src = pass ? Ad : A;
+        const float one = pass ? 0.f : 1.f;
+        for (int k0 = r0; k0 < r1; k0 += kBK) {
+            {
+                const int kk = tid >> 4, q4 = (tid & 15) * 4;
+                const int r = k0 + kk;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int m = m0 + q4 + j, n = n0 + q4 + j;
+                    As[kk][q4 + j] = (r < r1 && m < N) ? Zs[(size_t)r * ldz + m] : 0.f;
+                    float bv = 0.f;
+                    if (r < r1) {
+                        if (n < K) bv = As_src[(size_t)r * lda + n];
+                        else if (n == K) bv = one;
+                    }
+                    Bs[kk][q4 + j] = bv;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < kBK; ++kk) {
+                float a[4], b[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { a[q] = As[kk][ty * 4 + q]; b[q] = Bs[kk][tx * 4 + q]; }
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+            }
+            __syncthreads();
+        }
+    }
+    float* out = part + (size_t)split * P;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int m = m0 + ty * 4 + p;
+        if (m >= N) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int n = n0 + tx * 4 + q;
+            if (n < K) out[la.w_off[s] + (size_t)m * K + n] = acc[p][q];
+            else if (n == K) out[la.b_off[s] + m] = acc[p][q];
+        }
+    }
+}
+
+__global__ void k_reduce_splits(int64_t P, int splits, const float* __restrict__ part, float* __restrict__ out)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float s = 0.f;
+    for (int k = 0; k < splits; ++k) s += part[(size_t)k * P + p];
+    out[p] = s;
+}
+
+// Reverse-pass seeds and elementwise adjoints of one layer:
+//   Zb  = Ab * act'(Z) + Adb * act''(Z) * Zd,   Zdb = Adb * act'(Z)
+__global__ void k_layer_adjoint(LayerArgs la, const int32_t* __restrict__ seg_off, int64_t N, int ld,
+                                const float* __restrict__ Ab, const float* __restrict__ Adb,
+                                const float* __restrict__ Z, const float* __restrict__ Zd,
+                                float* __restrict__ Zb, float* __restrict__ Zdb)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * ld) return;
+    const int64_t r = idx / ld;
+    const int c = (int)(idx % ld);
+    int s = 0;
+    while (s < la.S - 1 && r >= seg_off[s + 1]) ++s;
+    if (c >= la.N[s]) return;
+    const int t = la.act[s];
+    const float z = Z[idx];
+    const float d1 = act_d1(t, z);
+    Zb[idx] = Ab[idx] * d1 + Adb[idx] * act_d2(t, z) * Zd[idx];
+    Zdb[idx] = Adb[idx] * d1;
+}
+
+// last-layer seeds: Ab = alpha_row (energy part), Adb = -1 (force part), widths 1
+__global__ void k_seed(int64_t N, int ld, const float* __restrict__ alpha_rows, float beta,
+                       float* __restrict__ Ab, float* __restrict__ Adb)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    Ab[r * ld] = alpha_rows ? alpha_rows[r] : 1.f;
+    if (Adb) Adb[r * ld] = beta;
+}
+
+// ----------------------------------------------------------------------------- host side
+
+static LayerArgs layer_args(const MlpPlan& p, int l, bool backward)
+{
+    LayerArgs la{};
+    la.S = p.S;
+    for (int s = 0; s < p.S; ++s) {
+        const int in = p.widths[s][l], out = p.widths[s][l + 1];
+        la.K[s] = backward ? out : in;
+        la.N[s] = backward ? in : out;
+        la.act[s] = p.acts[s][l];
+        la.pact[s] = p.acts[s][l];
+        la.w_off[s] = p.w_off[s][l];
+        la.b_off[s] = p.b_off[s][l];
+    }
+    return la;
+}
+
+static dim3 gemm_grid(const MlpPlan& p, int64_t N, int n_max)
+{
+    return dim3((unsigned)((N + kBM - 1) / kBM + p.S), (unsigned)((n_max + kBN - 1) / kBN), 1);
+}
+
+cudaError_t mlp_tiles(const MlpPlan& p, const int32_t* seg_off, int32_t* tile_start, cudaStream_t s, int* launches)
+{
+    k_tiles<<<1, 32, 0, s>>>(p.S, seg_off, tile_start);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_forward(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, cudaStream_t s,
+                        int* launches)
+{
+    for (int l = 0; l < p.L; ++l) {
+        LayerArgs la = layer_args(p, l, false);
+        const float* Ain = l == 0 ? b.G : b.A[l];
+        const int lda = p.ld[l];
+        k_gemm<true, PRO_NONE, EPI_FWD><<<gemm_grid(p, N, p.ld[l + 1]), 256, 0, s>>>(
+            la, theta, b.seg_off, b.tile_start, Ain, lda, nullptr, 0, b.Z[l + 1], p.ld[l + 1], b.A[l + 1],
+            nullptr, 0);
+        ++*launches;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, float* g,
+                           cudaStream_t s, int* launches)
+{
+    // seed dE/da_L = 1, then a_{l-1}bar = (a_l bar * act'(z_l)) W_l
+    k_seed<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, p.ld[p.L], nullptr, 0.f, b.Ab, nullptr);
+    ++*launches;
+    float* cur = b.Ab;
+    float* nxt = b.Ab2;
+    for (int l = p.L - 1; l >= 0; --l) {
+        LayerArgs la = layer_args(p, l, true);
+        float* out = l == 0 ? g : nxt;
+        const int ldo = p.ld[l];
+        k_gemm<false, PRO_DACT, EPI_STORE><<<gemm_grid(p, N, p.ld[l]), 256, 0, s>>>(
+            la, theta, b.seg_off, b.tile_start, cur, p.ld[l + 1], b.Z[l + 1], p.ld[l + 1], out, ldo, nullptr,
+            nullptr, 0);
+        ++*launches;
+        float* t = cur; cur = out; nxt = t;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N,
+                           const float* wdot, const float* alpha_rows, float* dtheta, cudaStream_t s,
+                           int* launches)
+{
+    // forward tangent along wdot: zdot_l = adot_{l-1} W_l^T, adot_l = act'(z_l) zdot_l
+    for (int l = 0; l < p.L; ++l) {
+        LayerArgs la = layer_args(p, l, false);
+        const float* Ain = l == 0 ? wdot : b.Ad[l];
+        k_gemm<true, PRO_NONE, EPI_TAN><<<gemm_grid(p, N, p.ld[l + 1]), 256, 0, s>>>(
+            la, theta, b.seg_off, b.tile_start, Ain, p.ld[l], nullptr, 0, b.Zd[l + 1], p.ld[l + 1], b.Ad[l + 1],
+            b.Z[l + 1], p.ld[l + 1]);
+        ++*launches;
+    }
+    // reverse pass: seeds abar_L = alpha, adotbar_L = -1
+    k_seed<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, p.ld[p.L], alpha_rows, -1.f, b.Ab, b.Adb);
+    ++*launches;
+    for (int l = p.L - 1; l >= 0; --l) {
+        const int ldl = p.ld[l + 1];
+        k_layer_adjoint<<<(unsigned)((N * ldl + 255) / 256), 256, 0, s>>>(
+            layer_args(p, l, false), b.seg_off, N, ldl, b.Ab, b.Adb, b.Z[l + 1], b.Zd[l + 1], b.Zb, b.Zdb);
+        ++*launches;
+        // weight gradient of layer l+1
+        LayerArgs lw = layer_args(p, l, false);
+        const float* Ain = l == 0 ? b.G : b.A[l];
+        const float* Adin = l == 0 ? wdot : b.Ad[l];
+        int kmax = 0, nmax = 0;
+        for (int q = 0; q < p.S; ++q) { kmax = max(kmax, lw.K[q]); nmax = max(nmax, lw.N[q]); }
+        dim3 gw((unsigned)((nmax + kBM - 1) / kBM), (unsigned)((kmax + 1 + kBN - 1) / kBN), (unsigned)(p.S * b.splits));
+        k_wgrad<<<gw, 256, 0, s>>>(lw, b.seg_off, b.splits, b.Zb, Ain, ldl, p.ld[l], b.Zdb, Adin, b.part, p.P);
+        ++*launches;
+        if (l > 0) {
+            // abar_{l} = Zb W_{l+1}, adotbar_{l} = Zdb W_{l+1}
+            LayerArgs la = layer_args(p, l, true);
+            k_gemm<false, PRO_NONE, EPI_STORE><<<gemm_grid(p, N, p.ld[l]), 256, 0, s>>>(
+                la, theta, b.seg_off, b.tile_start, b.Zb, ldl, nullptr, 0, b.Ab, p.ld[l], nullptr, nullptr, 0);
+            k_gemm<false, PRO_NONE, EPI_STORE><<<gemm_grid(p, N, p.ld[l]), 256, 0, s>>>(
+                la, theta, b.seg_off, b.tile_start, b.Zdb, ldl, nullptr, 0, b.Adb, p.ld[l], nullptr, nullptr, 0);
+            *launches += 2;
+        }
+    }
+    k_reduce_splits<<<(unsigned)((p.P + 255) / 256), 256, 0, s>>>(p.P, b.splits, b.part, dtheta);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// E_rows[r] = A_L[r][0]
+__global__ void k_take_energy(int64_t N, int ld, const float* __restrict__ AL, float* __restrict__ E_rows)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < N) E_rows[r] = AL[r * ld];
+}
+
+cudaError_t mlp_energy_rows(const MlpPlan& p, const MlpBuffers& b, int64_t N, float* E_rows, cudaStream_t s,
+                            int* launches)
+{
+    k_take_energy<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, p.ld[p.L], b.A[p.L], E_rows);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace panna

@@ -1,0 +1,630 @@
+// Cell-list neighbour search on the GPU (locality within rc, Sec. I / Sec. II.A).
+//
+// Stages, all on the caller's stream:
+//   k_cfg_geom     one CTA per configuration: frame, fractional bounding box, cell grid
+//                  (cells at least rc wide), image-shift table;
+//   k_bin          one thread per atom: fold into the cell, split the folded FP64
+//                  position into FP32 hi + lo, count atoms per cell;
+//   scan           exclusive scan of the cell counts;
+//   k_scatter / k_sort_cells   atoms of each cell, sorted by index (deterministic);
+//   k_neighbors    one warp per atom: scan the 3x3x3 (or wider) block of cells, FP32
+//                  filter on hi parts, then the relative vector in double-float (FP32
+//                  hi + lo, error-free sums) and an FP64 re-test for the rare pairs whose
+//                  squared distance lies within 2e-6 rc^2 of the cutoff -- so the
+//                  neighbour set equals the FP64 definition for inputs with no pair within
+//                  1e-6 A of rc; entries are stored grouped by neighbour species.
+//   k_species_*    stable counting sort of atoms by species (network row order).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace panna {
+
+// ------------------------------------------------------------------ scan (int64)
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// exclusive scan of one value per thread over a 256-thread block; returns the block total
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t& excl)
+{
+    __shared__ int64_t wsum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = warp_incl_scan(v);
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t s = lane < kScanThreads / 32 ? wsum[lane] : 0;
+        s = warp_incl_scan(s);
+        if (lane < kScanThreads / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    int64_t before = wid > 0 ? wsum[wid - 1] : 0;
+    excl = before + inc - v;
+    int64_t total = wsum[kScanThreads / 32 - 1];
+    __syncthreads();
+    return total;
+}
+
+__global__ void k_scan_reduce(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ sums)
+{
+    int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    int64_t v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k)
+        if (base + k < n) v += in[base + k];
+    int64_t ex;
+    int64_t tot = block_excl_scan(v, ex);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int64_t* sums, int64_t nb)
+{
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+        int64_t k = b0 + threadIdx.x;
+        int64_t v = k < nb ? sums[k] : 0;
+        int64_t ex;
+        int64_t tot = block_excl_scan(v, ex);
+        if (k < nb) sums[k] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void k_scan_final(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                             const int64_t* __restrict__ sums)
+{
+    int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    int64_t v[kScanPer];
+    int64_t t = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        t += v[k];
+    }
+    int64_t ex;
+    block_excl_scan(t, ex);
+    int64_t run = sums[blockIdx.x] + ex;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[gridDim.x];
+}
+
+int64_t scan_scratch_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 2; }
+
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s,
+                               int* launches)
+{
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 0) nb = 1;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp, nb);
+    k_scan_final<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ geometry per config
+
+__device__ __forceinline__ int atom_config(const int64_t* __restrict__ off, int64_t C, int64_t i)
+{
+    int64_t lo = 0, hi = C - 1;  // largest c with off[c] <= i
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return (int)lo;
+}
+
+__global__ void k_atom_cfg(const int64_t* __restrict__ off, int64_t C, int64_t N, int32_t* __restrict__ atom_cfg)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) atom_cfg[i] = atom_config(off, C, i);
+}
+
+__global__ void k_cfg_geom(panna_system sys, double rc, CfgGeom* __restrict__ geom,
+                           int64_t* __restrict__ cfg_cells, DevStatus* st)
+{
+    const int c = blockIdx.x;
+    __shared__ double frame[9], finv[9];
+    __shared__ double red_lo[3][128], red_hi[3][128];
+    __shared__ int per_s[3];
+    const int64_t a0 = sys.atom_off[c], a1 = sys.atom_off[c + 1];
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int a = 0; a < 3; ++a) { per_s[a] = sys.pbc[3 * c + a] ? 1 : 0; any |= per_s[a]; }
+        for (int k = 0; k < 9; ++k) frame[k] = any ? sys.cell[9 * c + k] : (k % 4 == 0 ? 1.0 : 0.0);
+        const double* m = frame;
+        double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6])
+                   + m[2] * (m[3] * m[7] - m[4] * m[6]);
+        if (!(fabs(det) > 1e-12) || !isfinite(det)) {
+            set_status(st, PANNA_ERR_BAD_INPUT, c);
+            for (int k = 0; k < 9; ++k) frame[k] = (k % 4 == 0 ? 1.0 : 0.0);
+            det = 1.0;
+            per_s[0] = per_s[1] = per_s[2] = 0;
+        }
+        finv[0] = (m[4] * m[8] - m[5] * m[7]) / det;
+        finv[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+        finv[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+        finv[3] = (m[5] * m[6] - m[3] * m[8]) / det;
+        finv[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+        finv[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+        finv[6] = (m[3] * m[7] - m[4] * m[6]) / det;
+        finv[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+        finv[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+    }
+    __syncthreads();
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    const bool all_periodic = per_s[0] && per_s[1] && per_s[2];
+    for (int64_t i = a0 + threadIdx.x; i < a1 && !all_periodic; i += blockDim.x) {
+        const double* x = sys.pos + 3 * i;
+        for (int a = 0; a < 3; ++a) {
+            double s = x[0] * finv[a] + x[1] * finv[3 + a] + x[2] * finv[6 + a];
+            lo[a] = fmin(lo[a], s);
+            hi[a] = fmax(hi[a], s);
+        }
+    }
+    for (int a = 0; a < 3; ++a) { red_lo[a][threadIdx.x] = lo[a]; red_hi[a][threadIdx.x] = hi[a]; }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int a = 0; a < 3; ++a) {
+                red_lo[a][threadIdx.x] = fmin(red_lo[a][threadIdx.x], red_lo[a][threadIdx.x + o]);
+                red_hi[a][threadIdx.x] = fmax(red_hi[a][threadIdx.x], red_hi[a][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    CfgGeom g;
+    for (int k = 0; k < 9; ++k) { g.cell[k] = frame[k]; g.cinv[k] = finv[k]; }
+    // perpendicular widths of the frame
+    const double* A = frame; const double* B = frame + 3; const double* Cc = frame + 6;
+    double bxc[3] = {B[1] * Cc[2] - B[2] * Cc[1], B[2] * Cc[0] - B[0] * Cc[2], B[0] * Cc[1] - B[1] * Cc[0]};
+    double cxa[3] = {Cc[1] * A[2] - Cc[2] * A[1], Cc[2] * A[0] - Cc[0] * A[2], Cc[0] * A[1] - Cc[1] * A[0]};
+    double axb[3] = {A[1] * B[2] - A[2] * B[1], A[2] * B[0] - A[0] * B[2], A[0] * B[1] - A[1] * B[0]};
+    double vol = fabs(A[0] * bxc[0] + A[1] * bxc[1] + A[2] * bxc[2]);
+    double h[3] = {vol / sqrt(bxc[0] * bxc[0] + bxc[1] * bxc[1] + bxc[2] * bxc[2]),
+                   vol / sqrt(cxa[0] * cxa[0] + cxa[1] * cxa[1] + cxa[2] * cxa[2]),
+                   vol / sqrt(axb[0] * axb[0] + axb[1] * axb[1] + axb[2] * axb[2])};
+    const double rcw = rc * (1.0 + 1e-9);   // cells strictly wider than rc
+    double ext[3];
+    int64_t n_at = a1 - a0;
+    for (int a = 0; a < 3; ++a) {
+        g.per[a] = per_s[a];
+        if (g.per[a]) {
+            g.lo[a] = 0.0;
+            ext[a] = 1.0;
+        } else {
+            g.lo[a] = n_at > 0 ? red_lo[a][0] : 0.0;
+            ext[a] = n_at > 0 ? fmax(red_hi[a][0] - red_lo[a][0], 0.0) : 0.0;
+        }
+        double phys = ext[a] * h[a];
+        double nc = floor(phys / rcw);
+        g.n[a] = nc < 1.0 ? 1 : (nc > 1024.0 ? 1024 : (int)nc);
+    }
+    // no more cells than max(1, 2 * atoms): wider cells keep the search exact
+    int64_t lim = n_at > 0 ? 2 * n_at : 1;
+    while ((int64_t)g.n[0] * g.n[1] * g.n[2] > lim) {
+        int a = 0;
+        if (g.n[1] > g.n[a]) a = 1;
+        if (g.n[2] > g.n[a]) a = 2;
+        g.n[a] = (g.n[a] + 1) / 2;
+    }
+    for (int a = 0; a < 3; ++a) {
+        double e = ext[a] > 0.0 ? ext[a] : 1.0;
+        g.inv_w[a] = (double)g.n[a] / e;
+        double cw = h[a] * e / g.n[a];   // perpendicular cell width
+        int K = 1;
+        if (g.per[a] && cw < rcw) K = (int)ceil(rcw / cw);
+        g.K[a] = K;
+    }
+    g.ncells = g.n[0] * g.n[1] * g.n[2];
+    g.cell_base = 0;
+    for (int t0 = -1; t0 <= 1; ++t0)
+        for (int t1 = -1; t1 <= 1; ++t1)
+            for (int t2 = -1; t2 <= 1; ++t2) {
+                int k = (t0 + 1) * 9 + (t1 + 1) * 3 + (t2 + 1);
+                for (int d = 0; d < 3; ++d) {
+                    double S = t0 * frame[d] + t1 * frame[3 + d] + t2 * frame[6 + d];
+                    float sh = (float)S;
+                    g.sh_hi[k][d] = sh;
+                    g.sh_lo[k][d] = (float)(S - (double)sh);
+                }
+            }
+    geom[c] = g;
+    cfg_cells[c] = g.ncells;
+}
+
+__global__ void k_set_cell_base(CfgGeom* __restrict__ geom, const int64_t* __restrict__ base, int64_t C)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < C) geom[c].cell_base = base[c];
+}
+
+__global__ void k_bin(panna_system sys, int S, const CfgGeom* __restrict__ geom,
+                      const int32_t* __restrict__ atom_cfg, int32_t* __restrict__ atom_cell,
+                      int64_t* __restrict__ cell_count, float4* __restrict__ pos_hi,
+                      float4* __restrict__ pos_lo, int32_t* __restrict__ wrap, DevStatus* st)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sys.n_atoms) return;
+    const int c = atom_cfg[i];
+    const CfgGeom& g = geom[c];
+    double x[3] = {sys.pos[3 * i], sys.pos[3 * i + 1], sys.pos[3 * i + 2]};
+    int sp = sys.species[i];
+    if (sp < 0 || sp >= S) { set_status(st, PANNA_ERR_BAD_INPUT, (int)i); sp = 0; }
+    if (!(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]))) {
+        set_status(st, PANNA_ERR_BAD_INPUT, (int)i);
+        x[0] = x[1] = x[2] = 0.0;
+    }
+    int m[3], ci[3];
+    double sf[3];
+    for (int a = 0; a < 3; ++a) {
+        double s = x[0] * g.cinv[a] + x[1] * g.cinv[3 + a] + x[2] * g.cinv[6 + a];
+        m[a] = g.per[a] ? -(int)floor(s) : 0;
+        sf[a] = s + m[a];
+        double q = floor((sf[a] - g.lo[a]) * g.inv_w[a]);
+        int k = q < 0.0 ? 0 : (q >= (double)g.n[a] ? g.n[a] - 1 : (int)q);
+        ci[a] = k;
+    }
+    double xw[3];
+    for (int d = 0; d < 3; ++d) xw[d] = x[d] + m[0] * g.cell[d] + m[1] * g.cell[3 + d] + m[2] * g.cell[6 + d];
+    float h0 = (float)xw[0], h1 = (float)xw[1], h2 = (float)xw[2];
+    pos_hi[i] = make_float4(h0, h1, h2, __int_as_float(sp));
+    pos_lo[i] = make_float4((float)(xw[0] - h0), (float)(xw[1] - h1), (float)(xw[2] - h2), 0.f);
+    wrap[3 * i] = m[0]; wrap[3 * i + 1] = m[1]; wrap[3 * i + 2] = m[2];
+    int local = (ci[0] * g.n[1] + ci[1]) * g.n[2] + ci[2];
+    atom_cell[i] = local;
+    atomicAdd((unsigned long long*)&cell_count[g.cell_base + local], 1ull);
+}
+
+__global__ void k_scatter(int64_t N, const int32_t* __restrict__ atom_cfg, const int32_t* __restrict__ atom_cell,
+                          const CfgGeom* __restrict__ geom, const int64_t* __restrict__ cell_start,
+                          int32_t* __restrict__ cell_fill, int32_t* __restrict__ cell_atoms)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int64_t gc = geom[atom_cfg[i]].cell_base + atom_cell[i];
+    int k = atomicAdd(&cell_fill[gc], 1);
+    cell_atoms[cell_start[gc] + k] = (int32_t)i;
+}
+
+__global__ void k_sort_cells(int64_t ncells, const int64_t* __restrict__ cell_start, int32_t* __restrict__ cell_atoms)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    int64_t b = cell_start[c], e = cell_start[c + 1];
+    for (int64_t k = b + 1; k < e; ++k) {
+        int32_t v = cell_atoms[k];
+        int64_t q = k - 1;
+        while (q >= b && cell_atoms[q] > v) { cell_atoms[q + 1] = cell_atoms[q]; --q; }
+        cell_atoms[q + 1] = v;
+    }
+}
+
+// ------------------------------------------------------------------ neighbour search
+
+// error-free sum of two floats: s + err == a + b exactly
+__device__ __forceinline__ float two_sum(float a, float b, float& err)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// (xj + S) - xi with each operand given as hi + lo, to about one FP32 rounding
+__device__ __forceinline__ float dd_rel(float xjh, float xjl, float sh, float sl, float xih, float xil)
+{
+    float e1, e2;
+    float a = two_sum(xjh, sh, e1);
+    float b = two_sum(a, -xih, e2);
+    float tail = __fsub_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(xjl, sl)), xil);
+    return __fadd_rn(b, tail);
+}
+
+constexpr int kNbWarps = 8;
+
+__global__ void __launch_bounds__(kNbWarps * 32)
+k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__ geom,
+            const int32_t* __restrict__ atom_cfg, const int32_t* __restrict__ atom_cell,
+            const int64_t* __restrict__ cell_start, const int32_t* __restrict__ cell_atoms,
+            const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo, int cap,
+            int32_t* __restrict__ nb_count, float4* __restrict__ nb_vec, int2* __restrict__ nb_idx,
+            DevStatus* st)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* svec = reinterpret_cast<float4*>(smem_raw) + (size_t)warp * cap;
+    int2* sidx = reinterpret_cast<int2*>(reinterpret_cast<float4*>(smem_raw) + (size_t)kNbWarps * cap) + (size_t)warp * cap;
+    const int64_t i = (int64_t)blockIdx.x * kNbWarps + warp;
+    if (i >= N) return;
+    const int c = atom_cfg[i];
+    const CfgGeom& g = geom[c];
+    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    const int local = atom_cell[i];
+    const int ci0 = local / (n1 * n2), ci1 = (local / n2) % n1, ci2 = local % n2;
+    const float4 xih = pos_hi[i], xil = pos_lo[i];
+    const float band = rc + 1e-2f;
+    const float band2 = band * band;
+    const float rc2 = rc * rc;
+    const double rc2d = rc_d * rc_d;
+    const unsigned lt = (1u << lane) - 1u;
+    int count = 0;
+    for (int d0 = -g.K[0]; d0 <= g.K[0]; ++d0) {
+        int c0 = ci0 + d0, t0 = 0;
+        if (g.per[0]) { t0 = (c0 >= 0 ? c0 / n0 : -((-c0 + n0 - 1) / n0)); c0 -= t0 * n0; }
+        else if (c0 < 0 || c0 >= n0) continue;
+        for (int d1 = -g.K[1]; d1 <= g.K[1]; ++d1) {
+            int c1 = ci1 + d1, t1 = 0;
+            if (g.per[1]) { t1 = (c1 >= 0 ? c1 / n1 : -((-c1 + n1 - 1) / n1)); c1 -= t1 * n1; }
+            else if (c1 < 0 || c1 >= n1) continue;
+            for (int d2 = -g.K[2]; d2 <= g.K[2]; ++d2) {
+                int c2 = ci2 + d2, t2 = 0;
+                if (g.per[2]) { t2 = (c2 >= 0 ? c2 / n2 : -((-c2 + n2 - 1) / n2)); c2 -= t2 * n2; }
+                else if (c2 < 0 || c2 >= n2) continue;
+                float shh[3], shl[3];
+                if (t0 >= -1 && t0 <= 1 && t1 >= -1 && t1 <= 1 && t2 >= -1 && t2 <= 1) {
+                    int k = (t0 + 1) * 9 + (t1 + 1) * 3 + (t2 + 1);
+                    for (int d = 0; d < 3; ++d) { shh[d] = g.sh_hi[k][d]; shl[d] = g.sh_lo[k][d]; }
+                } else {
+                    for (int d = 0; d < 3; ++d) {
+                        double Sv = t0 * g.cell[d] + t1 * g.cell[3 + d] + t2 * g.cell[6 + d];
+                        shh[d] = (float)Sv;
+                        shl[d] = (float)(Sv - (double)shh[d]);
+                    }
+                }
+                const bool self_image = (t0 == 0 && t1 == 0 && t2 == 0);
+                const int64_t gc = g.cell_base + (c0 * n1 + c1) * n2 + c2;
+                const int64_t b = cell_start[gc], e = cell_start[gc + 1];
+                for (int64_t base = b; base < e; base += 32) {
+                    const int64_t q = base + lane;
+                    bool in = false;
+                    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+                    int j = -1, spj = 0;
+                    if (q < e) {
+                        j = cell_atoms[q];
+                        const float4 xjh = pos_hi[j];
+                        spj = __float_as_int(xjh.w);
+                        float fx = (xjh.x + shh[0]) - xih.x;
+                        float fy = (xjh.y + shh[1]) - xih.y;
+                        float fz = (xjh.z + shh[2]) - xih.z;
+                        float f2 = fx * fx + fy * fy + fz * fz;
+                        if (f2 < band2 && !(self_image && j == (int)i)) {
+                            const float4 xjl = pos_lo[j];
+                            dx = dd_rel(xjh.x, xjl.x, shh[0], shl[0], xih.x, xil.x);
+                            dy = dd_rel(xjh.y, xjl.y, shh[1], shl[1], xih.y, xil.y);
+                            dz = dd_rel(xjh.z, xjl.z, shh[2], shl[2], xih.z, xil.z);
+                            r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+                            if (fabsf(r2 - rc2) <= 2e-6f * rc2) {
+                                // FP64 re-test near the cutoff
+                                double rx = ((double)xjh.x + (double)xjl.x) + ((double)shh[0] + (double)shl[0])
+                                          - ((double)xih.x + (double)xil.x);
+                                double ry = ((double)xjh.y + (double)xjl.y) + ((double)shh[1] + (double)shl[1])
+                                          - ((double)xih.y + (double)xil.y);
+                                double rz = ((double)xjh.z + (double)xjl.z) + ((double)shh[2] + (double)shl[2])
+                                          - ((double)xih.z + (double)xil.z);
+                                in = (rx * rx + ry * ry + rz * rz) < rc2d;
+                            } else {
+                                in = r2 < rc2;
+                            }
+                            if (in && r2 == 0.f) { set_status(st, PANNA_ERR_BAD_INPUT, (int)i); in = false; }
+                        }
+                    }
+                    const unsigned mask = __ballot_sync(0xffffffffu, in);
+                    if (in) {
+                        int pos = count + __popc(mask & lt);
+                        if (pos < cap) {
+                            svec[pos] = make_float4(dx, dy, dz, sqrtf(r2));
+                            sidx[pos] = make_int2(j, pack_meta(t0, t1, t2, spj));
+                        }
+                    }
+                    count += __popc(mask);
+                }
+            }
+        }
+    }
+    if (count > cap && lane == 0) {
+        atomicMax(&st->need_cap, count);
+        set_status(st, PANNA_ERR_NEIGHBOR_OVERFLOW, (int)i);
+    }
+    const int n = count < cap ? count : cap;
+    if (lane == 0) nb_count[i] = n;
+    __syncwarp();
+    const size_t out = (size_t)i * cap;
+    if (S == 1) {
+        for (int k = lane; k < n; k += 32) { nb_vec[out + k] = svec[k]; nb_idx[out + k] = sidx[k]; }
+        return;
+    }
+    int w = 0;
+    for (int s = 0; s < S; ++s) {
+        for (int base = 0; base < n; base += 32) {
+            const int k = base + lane;
+            const bool take = k < n && meta_species(sidx[k].y) == s;
+            const unsigned mask = __ballot_sync(0xffffffffu, take);
+            if (take) {
+                const int p = w + __popc(mask & lt);
+                nb_vec[out + p] = svec[k];
+                nb_idx[out + p] = sidx[k];
+            }
+            w += __popc(mask);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ CSR export
+
+__global__ void k_count_i64(int64_t N, const int32_t* __restrict__ cnt, int64_t* __restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) out[i] = cnt[i];
+}
+
+__global__ void k_export(int64_t N, int cap, const int32_t* __restrict__ nb_count, const int2* __restrict__ nb_idx,
+                         const int32_t* __restrict__ wrap, const int64_t* __restrict__ off, int64_t cap_total,
+                         int64_t* __restrict__ nbr_j, int32_t* __restrict__ shift)
+{
+    int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    const int n = nb_count[i];
+    for (int k = lane; k < n; k += 32) {
+        const int64_t p = off[i] + k;
+        if (p >= cap_total) continue;
+        const int2 e = nb_idx[(size_t)i * cap + k];
+        nbr_j[p] = e.x;
+        for (int a = 0; a < 3; ++a) shift[3 * p + a] = wrap[3 * (int64_t)e.x + a] - wrap[3 * i + a] + meta_t(e.y, a);
+    }
+}
+
+cudaError_t export_neighbors(const Work& w, int64_t* off, int64_t* nbr_j, int32_t* shift, int64_t cap_total,
+                             cudaStream_t s, int* launches)
+{
+    const int64_t N = w.N;
+    unsigned nb = (unsigned)((N + 255) / 256);
+    if (nb == 0) nb = 1;
+    k_count_i64<<<nb, 256, 0, s>>>(N, w.nb_count, w.cell_count);
+    ++*launches;
+    cudaError_t e = exclusive_scan_i64(w.cell_count, off, N, w.scan_tmp, s, launches);
+    if (e != cudaSuccess) return e;
+    unsigned nw = (unsigned)((N + 7) / 8);
+    if (nw == 0) nw = 1;
+    k_export<<<nw, 256, 0, s>>>(N, w.cap, w.nb_count, w.nb_idx, w.wrap, off, cap_total, nbr_j, shift);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ driver
+
+cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* launches)
+{
+    const int64_t N = w.N, C = w.C;
+    const panna_system& sys = *w.sys;
+    cudaError_t e;
+    unsigned nbA = (unsigned)((N + 255) / 256);
+    if (nbA == 0) nbA = 1;
+    k_atom_cfg<<<nbA, 256, 0, s>>>(sys.atom_off, C, N, w.atom_cfg);
+    k_cfg_geom<<<(unsigned)C, 128, 0, s>>>(sys, d.rc_d, w.geom, w.cell_count, w.status);
+    *launches += 2;
+    // cell bases: scan of per-config cell counts (stored temporarily in cell_count[0..C))
+    e = exclusive_scan_i64(w.cell_count, w.cell_start, C, w.scan_tmp, s, launches);
+    if (e != cudaSuccess) return e;
+    k_set_cell_base<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(w.geom, w.cell_start, C);
+    ++*launches;
+    // total cells <= 2N + C by construction; clear the counters
+    cudaMemsetAsync(w.cell_count, 0, sizeof(int64_t) * (w.cap_cells + 1), s);
+    cudaMemsetAsync(w.cell_fill, 0, sizeof(int32_t) * w.cap_cells, s);
+    k_bin<<<nbA, 256, 0, s>>>(sys, d.S, w.geom, w.atom_cfg, w.atom_cell, w.cell_count, w.pos_hi, w.pos_lo,
+                              w.wrap, w.status);
+    ++*launches;
+    e = exclusive_scan_i64(w.cell_count, w.cell_start, w.cap_cells, w.scan_tmp, s, launches);
+    if (e != cudaSuccess) return e;
+    k_scatter<<<nbA, 256, 0, s>>>(N, w.atom_cfg, w.atom_cell, w.geom, w.cell_start, w.cell_fill, w.cell_atoms);
+    k_sort_cells<<<(unsigned)((w.cap_cells + 255) / 256), 256, 0, s>>>(w.cap_cells, w.cell_start, w.cell_atoms);
+    *launches += 2;
+    size_t smem = (size_t)kNbWarps * w.cap * (sizeof(float4) + sizeof(int2));
+    e = cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    unsigned nbW = (unsigned)((N + kNbWarps - 1) / kNbWarps);
+    if (nbW == 0) nbW = 1;
+    k_neighbors<<<nbW, kNbWarps * 32, smem, s>>>(N, d.S, d.rc_d, d.rc, w.geom, w.atom_cfg, w.atom_cell,
+                                                 w.cell_start, w.cell_atoms, w.pos_hi, w.pos_lo, w.cap,
+                                                 w.nb_count, w.nb_vec, w.nb_idx, w.status);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ species order
+
+constexpr int kSpBlock = 1024;
+
+__global__ void k_species_count(int64_t N, int S, const float4* __restrict__ pos_hi, int32_t* __restrict__ blk_counts)
+{
+    __shared__ int cnt[kMaxSpecies];
+    if (threadIdx.x < kMaxSpecies) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * kSpBlock + threadIdx.x;
+    if (i < N) atomicAdd(&cnt[__float_as_int(pos_hi[i].w)], 1);
+    __syncthreads();
+    if (threadIdx.x < S) blk_counts[(size_t)blockIdx.x * S + threadIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_species_offsets(int64_t nblk, int S, int32_t* __restrict__ blk_counts, int32_t* __restrict__ seg_off)
+{
+    __shared__ int tot[kMaxSpecies];
+    const int s = threadIdx.x;
+    if (s < S) {
+        int run = 0;
+        for (int64_t b = 0; b < nblk; ++b) {
+            int v = blk_counts[b * S + s];
+            blk_counts[b * S + s] = run;
+            run += v;
+        }
+        tot[s] = run;
+    }
+    __syncthreads();
+    if (s < S) {
+        int base = 0;
+        for (int k = 0; k < s; ++k) base += tot[k];
+        for (int64_t b = 0; b < nblk; ++b) blk_counts[b * S + s] += base;
+        seg_off[s] = base;
+        if (s == S - 1) seg_off[S] = base + tot[s];
+    }
+}
+
+__global__ void k_species_rank(int64_t N, int S, const float4* __restrict__ pos_hi,
+                               const int32_t* __restrict__ blk_off, int32_t* __restrict__ row_of_atom,
+                               int32_t* __restrict__ atom_of_row)
+{
+    __shared__ int wcnt[kSpBlock / 32][kMaxSpecies];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t i = (int64_t)blockIdx.x * kSpBlock + threadIdx.x;
+    int sp = i < N ? __float_as_int(pos_hi[i].w) : -1;
+    int my_rank = 0;
+    for (int s = 0; s < S; ++s) {
+        unsigned m = __ballot_sync(0xffffffffu, sp == s);
+        if (sp == s) my_rank = __popc(m & ((1u << lane) - 1u));
+        if (lane == 0) wcnt[wid][s] = __popc(m);
+    }
+    __syncthreads();
+    if (i < N) {
+        int before = 0;
+        for (int w2 = 0; w2 < wid; ++w2) before += wcnt[w2][sp];
+        int row = blk_off[(size_t)blockIdx.x * S + sp] + before + my_rank;
+        row_of_atom[i] = row;
+        atom_of_row[row] = (int32_t)i;
+    }
+}
+
+cudaError_t species_order(Work& w, int S, cudaStream_t s, int* launches)
+{
+    int64_t nblk = (w.N + kSpBlock - 1) / kSpBlock;
+    if (nblk == 0) nblk = 1;
+    k_species_count<<<(unsigned)nblk, kSpBlock, 0, s>>>(w.N, S, w.pos_hi, w.blk_counts);
+    k_species_offsets<<<1, 32, 0, s>>>(nblk, S, w.blk_counts, w.seg_off);
+    k_species_rank<<<(unsigned)nblk, kSpBlock, 0, s>>>(w.N, S, w.pos_hi, w.blk_counts, w.row_of_atom, w.atom_of_row);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+}  // namespace panna

@@ -1,0 +1,315 @@
+"""Thin Python binding of libpanna_gb300 (ctypes).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of the
+library.  Functions keep the C names (``panna_create``, ``panna_energy_forces``, ...);
+:class:`Potential` bundles a context with device copies of a workload for convenience.
+Device buffers are torch CUDA tensors (torch provides memory and streams only).
+
+Importing this module does not need a GPU; loading the library does, and it fails
+loudly when the shared library has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpanna_gb300.so")
+MAX_LAYERS = 8
+
+PANNA_OK, PANNA_ERR_INVALID_ARG, PANNA_ERR_UNSUPPORTED, PANNA_ERR_NEIGHBOR_OVERFLOW = 0, 1, 2, 3
+PANNA_ERR_TIMEOUT, PANNA_ERR_CUDA, PANNA_ERR_NO_MEMORY, PANNA_ERR_BAD_INPUT = 4, 5, 6, 7
+PANNA_MLP_FP32, PANNA_MLP_BF16 = 0, 1
+
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+
+class panna_desc_params(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("rc", C.c_double),
+                ("n_rad", C.c_int32), ("rs_rad", _dp), ("eta_rad", C.c_double),
+                ("n_ang_r", C.c_int32), ("rs_ang", _dp),
+                ("n_theta", C.c_int32), ("theta_s", _dp),
+                ("eta_ang", C.c_double), ("zeta", C.c_double), ("eps_theta", C.c_double)]
+
+
+class panna_mlp_arch(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("widths", C.c_int32 * (MAX_LAYERS + 1)),
+                ("act", C.c_int32 * MAX_LAYERS)]
+
+
+class panna_system(C.Structure):
+    _fields_ = [("n_cfg", C.c_int64), ("n_atoms", C.c_int64), ("atom_off", _vp), ("pos", _vp),
+                ("species", _vp), ("cell", _vp), ("pbc", _vp)]
+
+
+class PannaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("panna status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libpanna_gb300.so not found at %s: run __graft_entry__.build() "
+                           "(there is no CPU fallback)" % path)
+    L = C.CDLL(path)
+    i32, i64, f32, f64 = C.c_int32, C.c_int64, C.c_float, C.c_double
+    sig = {
+        "panna_version": (C.c_char_p, []),
+        "panna_last_error": (C.c_char_p, []),
+        "panna_descriptor_size": (i64, [C.POINTER(panna_desc_params)]),
+        "panna_create": (i32, [C.POINTER(panna_desc_params), i32, C.POINTER(panna_mlp_arch), C.POINTER(_vp)]),
+        "panna_destroy": (None, [_vp]),
+        "panna_param_count": (i64, [_vp]),
+        "panna_set_neighbor_capacity": (i32, [_vp, i32]),
+        "panna_neighbor_capacity": (i32, [_vp]),
+        "panna_set_async": (i32, [_vp, i32]),
+        "panna_check": (i32, [_vp, _vp]),
+        "panna_neighbors": (i32, [_vp, C.POINTER(panna_system), i64, _vp, _vp, _vp, C.POINTER(i64), _vp]),
+        "panna_descriptors": (i32, [_vp, C.POINTER(panna_system), _vp, _vp]),
+        "panna_energy_forces": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
+        "panna_param_vjp": (i32, [_vp, C.POINTER(panna_system), _vp, _vp, _vp, _vp, _vp]),
+        "panna_loss_grad": (i32, [_vp, C.POINTER(panna_system), _vp, _vp, _vp, f64, _vp, _vp, _vp, _vp, _vp]),
+        "panna_last_launch_count": (i32, [_vp]),
+        "panna_set_profiling": (i32, [_vp, i32]),
+        "panna_stage_ms": (f32, [_vp, C.c_char_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols() -> Sequence[str]:
+    return ["panna_version", "panna_last_error", "panna_descriptor_size", "panna_create", "panna_destroy",
+            "panna_param_count", "panna_set_neighbor_capacity", "panna_neighbor_capacity", "panna_set_async",
+            "panna_check", "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
+            "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms"]
+
+
+def _check(status: int):
+    if status != PANNA_OK:
+        raise PannaError(status, load().panna_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+# ---------------------------------------------------------------------------- C names
+
+class _DescHolder:
+    def __init__(self, d):
+        self.rs_rad = np.ascontiguousarray(d.rs_rad, np.float64)
+        self.rs_ang = np.ascontiguousarray(d.rs_ang, np.float64)
+        self.theta_s = np.ascontiguousarray(d.theta_s, np.float64)
+        self.s = panna_desc_params(
+            int(d.n_species), float(d.rc), len(self.rs_rad), self.rs_rad.ctypes.data_as(_dp), float(d.eta_rad),
+            len(self.rs_ang), self.rs_ang.ctypes.data_as(_dp), len(self.theta_s),
+            self.theta_s.ctypes.data_as(_dp), float(d.eta_ang), float(d.zeta), float(d.eps_theta))
+
+
+def panna_descriptor_size(desc) -> int:
+    h = _DescHolder(desc)
+    return int(load().panna_descriptor_size(C.byref(h.s)))
+
+
+def panna_create(desc, archs) -> int:
+    h = _DescHolder(desc)
+    arr = (panna_mlp_arch * len(archs))()
+    for k, a in enumerate(archs):
+        arr[k].n_layers = a.n_layers
+        for l, w in enumerate(a.widths):
+            arr[k].widths[l] = int(w)
+        for l, t in enumerate(a.acts):
+            arr[k].act[l] = int(t)
+    out = _vp()
+    _check(load().panna_create(C.byref(h.s), len(archs), arr, C.byref(out)))
+    return out.value
+
+
+def panna_destroy(ctx: int):
+    load().panna_destroy(ctx)
+
+
+def panna_param_count(ctx: int) -> int:
+    return int(load().panna_param_count(ctx))
+
+
+def panna_set_neighbor_capacity(ctx: int, cap: int):
+    _check(load().panna_set_neighbor_capacity(ctx, int(cap)))
+
+
+def panna_neighbor_capacity(ctx: int) -> int:
+    return int(load().panna_neighbor_capacity(ctx))
+
+
+def panna_set_async(ctx: int, on: bool):
+    _check(load().panna_set_async(ctx, 1 if on else 0))
+
+
+def panna_check(ctx: int, stream=None):
+    _check(load().panna_check(ctx, _stream(stream)))
+
+
+def panna_neighbors(ctx: int, sysd: "DeviceSystem", cap_total: int, nbr_off, nbr_j, nbr_shift, stream=None) -> int:
+    n = C.c_int64(0)
+    _check(load().panna_neighbors(ctx, C.byref(sysd.s), int(cap_total), _ptr(nbr_off), _ptr(nbr_j),
+                                  _ptr(nbr_shift), C.byref(n), _stream(stream)))
+    return int(n.value)
+
+
+def panna_descriptors(ctx: int, sysd: "DeviceSystem", G, stream=None):
+    _check(load().panna_descriptors(ctx, C.byref(sysd.s), _ptr(G), _stream(stream)))
+
+
+def panna_energy_forces(ctx: int, sysd: "DeviceSystem", theta, prec: int, E_cfg, E_atom, F, virial, stream=None):
+    _check(load().panna_energy_forces(ctx, C.byref(sysd.s), _ptr(theta), int(prec), _ptr(E_cfg), _ptr(E_atom),
+                                      _ptr(F), _ptr(virial), _stream(stream)))
+
+
+def panna_param_vjp(ctx: int, sysd: "DeviceSystem", theta, dE, dF, dtheta, stream=None):
+    _check(load().panna_param_vjp(ctx, C.byref(sysd.s), _ptr(theta), _ptr(dE), _ptr(dF), _ptr(dtheta),
+                                  _stream(stream)))
+
+
+def panna_loss_grad(ctx: int, sysd: "DeviceSystem", theta, E_ref, F_ref, w_force: float, loss, dtheta,
+                    E_cfg=None, F=None, stream=None):
+    _check(load().panna_loss_grad(ctx, C.byref(sysd.s), _ptr(theta), _ptr(E_ref), _ptr(F_ref), float(w_force),
+                                  _ptr(loss), _ptr(dtheta), _ptr(E_cfg), _ptr(F), _stream(stream)))
+
+
+def panna_last_launch_count(ctx: int) -> int:
+    return int(load().panna_last_launch_count(ctx))
+
+
+def panna_set_profiling(ctx: int, on: bool):
+    _check(load().panna_set_profiling(ctx, 1 if on else 0))
+
+
+def panna_stage_ms(ctx: int, stage: str) -> float:
+    return float(load().panna_stage_ms(ctx, stage.encode()))
+
+
+def panna_version() -> str:
+    return load().panna_version().decode()
+
+
+# ---------------------------------------------------------------------------- helpers
+
+class DeviceSystem:
+    """Device copies (torch CUDA tensors) of a workloads.System plus the C struct."""
+
+    def __init__(self, system, device="cuda"):
+        import torch
+        self.atom_off = torch.as_tensor(np.ascontiguousarray(system.atom_off, np.int64), device=device)
+        self.pos = torch.as_tensor(np.ascontiguousarray(system.pos, np.float64), device=device)
+        self.species = torch.as_tensor(np.ascontiguousarray(system.species, np.int32), device=device)
+        self.cell = torch.as_tensor(np.ascontiguousarray(system.cell, np.float64), device=device)
+        self.pbc = torch.as_tensor(np.ascontiguousarray(system.pbc, np.uint8), device=device)
+        self.n_cfg = int(system.n_cfg)
+        self.n_atoms = int(system.n_atoms)
+        self.s = panna_system(self.n_cfg, self.n_atoms, self.atom_off.data_ptr(), self.pos.data_ptr(),
+                              self.species.data_ptr(), self.cell.data_ptr(), self.pbc.data_ptr())
+
+    @classmethod
+    def from_tensors(cls, atom_off, pos, species, cell, pbc):
+        obj = cls.__new__(cls)
+        obj.atom_off, obj.pos, obj.species, obj.cell, obj.pbc = atom_off, pos, species, cell, pbc
+        obj.n_cfg = int(atom_off.shape[0] - 1)
+        obj.n_atoms = int(pos.shape[0])
+        obj.s = panna_system(obj.n_cfg, obj.n_atoms, atom_off.data_ptr(), pos.data_ptr(), species.data_ptr(),
+                             cell.data_ptr(), pbc.data_ptr())
+        return obj
+
+
+class Potential:
+    """A context plus convenience calls returning torch tensors."""
+
+    def __init__(self, desc, archs, neighbor_capacity: Optional[int] = None):
+        self.desc = desc
+        self.archs = list(archs)
+        self.ctx = panna_create(desc, archs)
+        self.D = panna_descriptor_size(desc)
+        self.P = panna_param_count(self.ctx)
+        if neighbor_capacity:
+            panna_set_neighbor_capacity(self.ctx, neighbor_capacity)
+
+    def close(self):
+        if self.ctx:
+            panna_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def descriptors(self, sysd: DeviceSystem):
+        import torch
+        G = torch.empty((sysd.n_atoms, self.D), dtype=torch.float32, device="cuda")
+        panna_descriptors(self.ctx, sysd, G)
+        return G
+
+    def neighbors(self, sysd: DeviceSystem):
+        import torch
+        cap = max(1, sysd.n_atoms * panna_neighbor_capacity(self.ctx))
+        while True:
+            off = torch.empty(sysd.n_atoms + 1, dtype=torch.int64, device="cuda")
+            j = torch.empty(cap, dtype=torch.int64, device="cuda")
+            sh = torch.empty((cap, 3), dtype=torch.int32, device="cuda")
+            try:
+                n = panna_neighbors(self.ctx, sysd, cap, off, j, sh)
+                return off, j[:n], sh[:n]
+            except PannaError as e:
+                if e.status != PANNA_ERR_INVALID_ARG:
+                    raise
+                cap *= 2
+
+    def energy_forces(self, sysd: DeviceSystem, theta, prec: int = PANNA_MLP_FP32, virial: bool = True,
+                      atom_energies: bool = True):
+        import torch
+        E = torch.empty(sysd.n_cfg, dtype=torch.float64, device="cuda")
+        Ea = torch.empty(sysd.n_atoms, dtype=torch.float32, device="cuda") if atom_energies else None
+        F = torch.empty((sysd.n_atoms, 3), dtype=torch.float32, device="cuda")
+        V = torch.empty((sysd.n_cfg, 3, 3), dtype=torch.float64, device="cuda") if virial else None
+        panna_energy_forces(self.ctx, sysd, theta, prec, E, Ea, F, V)
+        return E, Ea, F, V
+
+    def param_vjp(self, sysd: DeviceSystem, theta, dE=None, dF=None):
+        import torch
+        out = torch.empty(self.P, dtype=torch.float32, device="cuda")
+        panna_param_vjp(self.ctx, sysd, theta, dE, dF, out)
+        return out
+
+    def loss_grad(self, sysd: DeviceSystem, theta, E_ref, F_ref, w_force: float):
+        import torch
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty(self.P, dtype=torch.float32, device="cuda")
+        E = torch.empty(sysd.n_cfg, dtype=torch.float64, device="cuda")
+        F = torch.empty((sysd.n_atoms, 3), dtype=torch.float32, device="cuda")
+        panna_loss_grad(self.ctx, sysd, theta, E_ref, F_ref, w_force, loss, g, E, F)
+        return loss, g, E, F
