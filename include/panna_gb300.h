@@ -162,6 +162,16 @@ int32_t panna_neighbor_capacity(const panna_ctx* ctx);
  */
 panna_status panna_set_async(panna_ctx* ctx, int32_t async);
 
+/*
+ * Arithmetic of the angular descriptor terms (descriptor, adjoint, JVP):
+ *   0 = automatic (default): extended precision with FP32 networks, plain FP32 with BF16;
+ *   1 = extended: unit vectors, cos/sin of the angle and (1 + cos(theta - theta_m))/2
+ *       carried as pairs of floats (about 4x smaller error under the zeta-th power,
+ *       about twice the arithmetic);
+ *   2 = plain FP32.
+ */
+panna_status panna_set_angular_precision(panna_ctx* ctx, int32_t mode);
+
 /* Synchronise `stream` and return (and clear) the device status word. */
 panna_status panna_check(panna_ctx* ctx, panna_stream_t stream);
 

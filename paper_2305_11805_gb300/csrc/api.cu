@@ -72,6 +72,7 @@ struct panna_ctx {
     int32_t cap = 64;
     int async = 0;
     int profiling = 0;
+    int ang_mode = 0;
     int last_launches = 0;
     Arena ws;
     DevStatus* h_status = nullptr;   // pinned
@@ -270,20 +271,23 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     int& nl = c->last_launches;
     const int64_t N = sys->n_atoms;
     const bool grad = rq.train || rq.vjp;
+    // FP32 networks get the extended-precision angular terms (force tolerance 1e-5 of RMS);
+    // BF16 networks (tolerance 1e-2) the plain FP32 form
+    const bool acc = c->ang_mode == 1 || (c->ang_mode == 0 && rq.prec == PANNA_MLP_FP32);
     for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
     CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
     stage_mark(c, 0, s);
     CU(build_neighbors(L.w, c->d, s, &nl));
     if (rq.G_out) {
         stage_mark(c, 1, s);
-        CU(launch_descriptor(L.w, c->d, rq.G_out, nullptr, s, &nl));
+        CU(launch_descriptor(L.w, c->d, rq.G_out, nullptr, c->ang_mode != 2, s, &nl));
         if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
         return PANNA_OK;
     }
     CU(species_order(L.w, c->d.S, s, &nl));
     CU(mlp_tiles(c->plan, L.w.seg_off, L.mb.tile_start, s, &nl));
     stage_mark(c, 1, s);
-    CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, s, &nl));
+    CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl));
     stage_mark(c, 2, s);
     CU(mlp_forward(c->plan, L.mb, rq.theta, N, s, &nl));
     CU(mlp_energy_rows(c->plan, L.mb, N, L.E_rows, s, &nl));
@@ -294,7 +298,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl));
         stage_mark(c, 3, s);
         CU(cudaMemsetAsync(F, 0, sizeof(float) * 3 * N, s));
-        CU(launch_adjoint(L.w, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, s, &nl));
+        CU(launch_adjoint(L.w, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, acc, s, &nl));
     }
     stage_mark(c, 4, s);
     CU(launch_cfg_reduce(L.w, L.E_rows, (rq.virial && need_forces) ? L.vir_atom : nullptr, E_cfg, rq.virial,
@@ -314,7 +318,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         CU(launch_row_scale(L.w, alpha, L.alpha_rows, s, &nl));
         stage_mark(c, 5, s);
         if (u) {
-            CU(launch_jvp(L.w, c->d, u, L.wdot, s, &nl));
+            CU(launch_jvp(L.w, c->d, u, L.wdot, acc, s, &nl));
         } else {
             CU(cudaMemsetAsync(L.wdot, 0, sizeof(float) * (size_t)N * c->d.D, s));
         }
@@ -396,9 +400,13 @@ panna_status panna_create(const panna_desc_params* p, int32_t n_archs, const pan
     for (int k = 0; k < p->n_rad; ++k) c->d.rs_rad[k] = (float)p->rs_rad[k];
     for (int k = 0; k < p->n_ang_r; ++k) c->d.rs_ang[k] = (float)p->rs_ang[k];
     for (int k = 0; k < p->n_theta; ++k) {
-        c->d.half_cos_t[k] = (float)(0.5 * cos(p->theta_s[k]));
-        c->d.half_sin_t[k] = (float)(0.5 * sin(p->theta_s[k]));
+        const double hc = 0.5 * cos(p->theta_s[k]), hs = 0.5 * sin(p->theta_s[k]);
+        c->d.half_cos_t[k] = (float)hc;
+        c->d.half_sin_t[k] = (float)hs;
+        c->d.half_cos_lo[k] = (float)(hc - (double)(float)hc);
+        c->d.half_sin_lo[k] = (float)(hs - (double)(float)hs);
     }
+    c->d.eps_theta_lo = (float)(p->eps_theta - (double)(float)p->eps_theta);
     MlpPlan& pl = c->plan;
     pl.S = d.S;
     pl.L = archs[0].n_layers;
@@ -470,6 +478,13 @@ panna_status panna_set_async(panna_ctx* c, int32_t async)
 {
     if (!c) return fail(PANNA_ERR_INVALID_ARG, "null context");
     c->async = async ? 1 : 0;
+    return PANNA_OK;
+}
+
+panna_status panna_set_angular_precision(panna_ctx* c, int32_t mode)
+{
+    if (!c || mode < 0 || mode > 2) return fail(PANNA_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+    c->ang_mode = mode;
     return PANNA_OK;
 }
 

@@ -38,8 +38,11 @@ struct DescDev {
     double rc_d;
     float rs_rad[kMaxRad];
     float rs_ang[kMaxAngR];
-    float half_cos_t[kMaxTheta];   // cos(theta_m) / 2
+    float half_cos_t[kMaxTheta];   // cos(theta_m) / 2 (float nearest)
     float half_sin_t[kMaxTheta];   // sin(theta_m) / 2
+    float half_cos_lo[kMaxTheta];  // remainders: exact value - float value
+    float half_sin_lo[kMaxTheta];
+    float eps_theta_lo;
 };
 
 // Geometry of one configuration as binned on the device.
@@ -102,11 +105,13 @@ cudaError_t species_order(Work& w, int S, cudaStream_t s, int* launches);
 cudaError_t export_neighbors(const Work& w, int64_t* off, int64_t* nbr_j, int32_t* shift, int64_t cap_total, cudaStream_t s, int* launches);
 
 // descriptor family (descriptor.cu); row_map == nullptr writes row i for atom i
-cudaError_t launch_descriptor(const Work& w, const DescDev& d, float* G_rows, const int32_t* row_map, cudaStream_t s,
-                              int* launches);
-cudaError_t launch_adjoint(const Work& w, const DescDev& d, const float* g_rows, float* F, float* vir_atom,
+// acc selects the extended-precision angular evaluation (see descriptor.cu)
+cudaError_t launch_descriptor(const Work& w, const DescDev& d, float* G_rows, const int32_t* row_map, bool acc,
+                              cudaStream_t s, int* launches);
+cudaError_t launch_adjoint(const Work& w, const DescDev& d, const float* g_rows, float* F, float* vir_atom, bool acc,
                            cudaStream_t s, int* launches);
-cudaError_t launch_jvp(const Work& w, const DescDev& d, const float* u, float* wdot_rows, cudaStream_t s, int* launches);
+cudaError_t launch_jvp(const Work& w, const DescDev& d, const float* u, float* wdot_rows, bool acc, cudaStream_t s,
+                       int* launches);
 
 // reductions (reduce.cu)
 int cfg_chunks(int64_t N, int64_t C);

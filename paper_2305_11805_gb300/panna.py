@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
         "panna_neighbor_capacity": (i32, [_vp]),
         "panna_set_async": (i32, [_vp, i32]),
         "panna_check": (i32, [_vp, _vp]),
+        "panna_set_angular_precision": (i32, [_vp, i32]),
         "panna_neighbors": (i32, [_vp, C.POINTER(panna_system), i64, _vp, _vp, _vp, C.POINTER(i64), _vp]),
         "panna_descriptors": (i32, [_vp, C.POINTER(panna_system), _vp, _vp]),
         "panna_energy_forces": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
@@ -96,7 +97,7 @@ def load(path: str = LIB_PATH):
 def exported_symbols() -> Sequence[str]:
     return ["panna_version", "panna_last_error", "panna_descriptor_size", "panna_create", "panna_destroy",
             "panna_param_count", "panna_set_neighbor_capacity", "panna_neighbor_capacity", "panna_set_async",
-            "panna_check", "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
+            "panna_check", "panna_set_angular_precision", "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms"]
 
 
@@ -168,6 +169,10 @@ def panna_neighbor_capacity(ctx: int) -> int:
 
 def panna_set_async(ctx: int, on: bool):
     _check(load().panna_set_async(ctx, 1 if on else 0))
+
+
+def panna_set_angular_precision(ctx: int, mode: int):
+    _check(load().panna_set_angular_precision(ctx, int(mode)))
 
 
 def panna_check(ctx: int, stream=None):

@@ -9,7 +9,7 @@ from paper_2305_11805_gb300 import workloads as W
 TOL_F_FP32 = 1e-5        # max |dF| / RMS(F_oracle)
 TOL_F_BF16 = 1e-2
 TOL_E = 1e-5             # |dE_c| / sum_i |E_i|
-TOL_G = 1e-5             # per descriptor component, relative to the component's max
+TOL_G = 1e-5             # per descriptor component, relative to its species block's max
 TOL_DTHETA = 1e-4        # per layer: max |d dW| / max |dW|
 
 
@@ -25,10 +25,27 @@ def gpu_neighbor_table(pot, sysd):
     return sorted_pairs(i, j.cpu().numpy(), sh.cpu().numpy())
 
 
-def descriptor_error(G, Go):
-    colmax = np.abs(Go).max(0)
+def block_scales(desc, Go):
+    """Max |G| over each species block (radial block per species, angular block per species
+    pair), broadcast to the block's components."""
+    colmax = np.abs(Go).max(0) if len(Go) else np.zeros(desc.D)
+    out = np.empty(desc.D)
+    S, nr, na = desc.n_species, desc.n_rad, desc.n_theta * desc.n_ang_r
+    edges = [s * nr for s in range(S + 1)] + [S * nr + b * na for b in range(1, S * (S + 1) // 2 + 1)]
+    for a, b in zip(edges[:-1], edges[1:]):
+        out[a:b] = colmax[a:b].max() if b > a else 0.0
+    return out
+
+
+def descriptor_error(G, Go, desc=None, where=False):
+    """max |G - Go| relative to the largest value of the component's species block."""
+    scale = block_scales(desc, Go) if desc is not None else np.abs(Go).max(0)
     floor = 1e-6 * max(np.abs(Go).max(), 1e-30)
-    return float((np.abs(G - Go) / np.maximum(colmax, floor)).max())
+    rel = np.abs(G - Go) / np.maximum(scale, floor)
+    if where:
+        i, c = np.unravel_index(np.argmax(rel), rel.shape)
+        return float(rel.max()), int(i), int(c), float(scale[c])
+    return float(rel.max())
 
 
 def force_error(F, Fo):

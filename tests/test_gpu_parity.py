@@ -61,8 +61,10 @@ def test_descriptors_match_oracle(torch_cuda, name):
     sysd = P.DeviceSystem(wl.system)
     G = pot.descriptors(sysd).cpu().numpy().astype(np.float64)
     Go = O.workload_batch(wl, want_G=True)["G"]
-    err = H.descriptor_error(G, Go)
-    print("%s descriptor max rel err %.3g" % (name, err))
+    err, ai, ac, cmax = H.descriptor_error(G, Go, wl.desc, where=True)
+    col = H.descriptor_error(G, Go)
+    print("%s descriptor max err %.3g of block max (atom %d, column %d of %d, block max %.3g);"
+          " per-column %.3g" % (name, err, ai, ac, wl.desc.D, cmax, col))
     assert err <= H.TOL_G
 
 
