@@ -79,6 +79,8 @@ struct panna_ctx {
     cudaEvent_t ev[kNumStages + 1] = {};
     float stage_ms[kNumStages] = {};
     bool stage_seen[kNumStages] = {};
+    int stage_order[kNumStages + 1] = {};   // stages in the order they were marked
+    int n_marked = 0;
 };
 
 // ------------------------------------------------------------------ workspace layout
@@ -211,6 +213,7 @@ void stage_mark(panna_ctx* c, int k, cudaStream_t s)
     if (c->profiling) {
         cudaEventRecord(c->ev[k], s);
         c->stage_seen[k] = true;
+        if (c->n_marked <= kNumStages) c->stage_order[c->n_marked++] = k;
     }
 }
 
@@ -231,15 +234,15 @@ panna_status collect(panna_ctx* c, const Layout& L, cudaStream_t s, int* need)
                 c->h_status->bad_index);
 }
 
+// each stage lasts from its mark to the next mark in time (the last one to the end event)
 void finish_profile(panna_ctx* c)
 {
     if (!c->profiling) return;
     cudaEventSynchronize(c->ev[kNumStages]);
-    int prev = -1;
-    for (int k = 0; k <= kNumStages; ++k) {
-        if (k < kNumStages && !c->stage_seen[k]) continue;
-        if (prev >= 0) cudaEventElapsedTime(&c->stage_ms[prev], c->ev[prev], c->ev[k]);
-        prev = k;
+    for (int q = 0; q < c->n_marked; ++q) {
+        const int k = c->stage_order[q];
+        const int nxt = q + 1 < c->n_marked ? c->stage_order[q + 1] : kNumStages;
+        cudaEventElapsedTime(&c->stage_ms[k], c->ev[k], c->ev[nxt]);
     }
 }
 
@@ -275,6 +278,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     // BF16 networks (tolerance 1e-2) the plain FP32 form
     const bool acc = c->ang_mode == 1 || (c->ang_mode == 0 && rq.prec == PANNA_MLP_FP32);
     for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
+    c->n_marked = 0;
     CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
     stage_mark(c, 0, s);
     CU(build_neighbors(L.w, c->d, s, &nl));
