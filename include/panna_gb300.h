@@ -244,6 +244,29 @@ int32_t panna_last_launch_count(const panna_ctx* ctx);
 panna_status panna_set_profiling(panna_ctx* ctx, int32_t on);
 float panna_stage_ms(const panna_ctx* ctx, const char* stage);
 
+/*
+ * Descriptors G [n_atoms*D] FP32 (device, row i = atom i) of a small batch, computed
+ * without allocating any memory: no context, no cudaMalloc, no cudaFree.  The paper has
+ * no counterpart; this entry point exists for callers that cannot allocate device memory
+ * -- a host program whose memory pool already owns all of the GPU's memory, or a callback
+ * (such as a force call from inside another code's time step) in which new device
+ * allocations are not allowed.  Same parameters and result as panna_descriptors.
+ *
+ * Scratch (cell lists, neighbour lists, a status word) lives in one static device array
+ * of 32 MiB that every GPU which loads this library holds until the process exits.  It
+ * takes about 100 bytes per atom and 900 per configuration for binning, plus 24 bytes per
+ * neighbour slot (at most 256 slots per atom, as many as fit): roughly 20,000 atoms with
+ * 64 neighbours each.  A batch that does not leave room for 8 slots per atom is rejected
+ * with PANNA_ERR_INVALID_ARG before any work; an atom with more neighbours than the slots
+ * that fit gives PANNA_ERR_NEIGHBOR_OVERFLOW.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call uses the same array and clears what must start at
+ * zero: calls that overlap on the GPU (other streams, other host threads) race.  The call
+ * synchronises `stream`; errors are also reported through panna_last_error().
+ */
+panna_status panna_descriptors_static(const panna_desc_params* desc, const panna_system* sys, float* G,
+                                      panna_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,8 @@ static panna_status fail(panna_status st, const char* fmt, ...)
     return st;
 }
 
+void panna::set_last_error_message(const char* msg) { g_last_error = msg; }
+
 #define CU(call)                                                                              \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \

@@ -123,4 +123,7 @@ cudaError_t launch_loss(const Work& w, const double* E_cfg, const double* E_ref,
                         int* launches);
 cudaError_t launch_row_scale(const Work& w, const double* alpha_cfg, float* alpha_rows, cudaStream_t s, int* launches);
 
+// message returned by panna_last_error() on this thread (api.cu)
+void set_last_error_message(const char* msg);
+
 }  // namespace panna

@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
         "panna_last_launch_count": (i32, [_vp]),
         "panna_set_profiling": (i32, [_vp, i32]),
         "panna_stage_ms": (f32, [_vp, C.c_char_p]),
+        "panna_descriptors_static": (i32, [C.POINTER(panna_desc_params), C.POINTER(panna_system), _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -98,7 +99,8 @@ def exported_symbols() -> Sequence[str]:
     return ["panna_version", "panna_last_error", "panna_descriptor_size", "panna_create", "panna_destroy",
             "panna_param_count", "panna_set_neighbor_capacity", "panna_neighbor_capacity", "panna_set_async",
             "panna_check", "panna_set_angular_precision", "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
-            "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms"]
+            "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
+            "panna_descriptors_static"]
 
 
 def _check(status: int):
@@ -216,6 +218,12 @@ def panna_set_profiling(ctx: int, on: bool):
 
 def panna_stage_ms(ctx: int, stage: str) -> float:
     return float(load().panna_stage_ms(ctx, stage.encode()))
+
+
+def panna_descriptors_static(desc, sysd: "DeviceSystem", G, stream=None):
+    """Descriptors into G without any device allocation (static scratch; see the header)."""
+    h = _DescHolder(desc)
+    _check(load().panna_descriptors_static(C.byref(h.s), C.byref(sysd.s), _ptr(G), _stream(stream)))
 
 
 def panna_version() -> str:
