@@ -1,7 +1,7 @@
 // Cell-list neighbour search on the GPU (locality within rc, Sec. I / Sec. II.A).
 //
 // Stages, all on the caller's stream:
-//   k_cfg_geom     one CTA per configuration: frame, fractional bounding box, cell grid
+//   k_cfg_geom     one warp per configuration: frame, fractional bounding box, cell grid
 //                  (cells at least rc wide), image-shift table;
 //   k_bin          one thread per atom: fold into the cell, split the folded FP64
 //                  position into FP32 hi + lo, count atoms per cell;
@@ -142,60 +142,81 @@ __global__ void k_atom_cfg(const int64_t* __restrict__ off, int64_t C, int64_t N
     if (i < N) atom_cfg[i] = atom_config(off, C, i);
 }
 
-__global__ void k_cfg_geom(panna_system sys, double rc, CfgGeom* __restrict__ geom,
-                           int64_t* __restrict__ cfg_cells, DevStatus* st)
+// One warp per configuration (kCfgWarps per block).
+constexpr int kCfgWarps = 8;
+
+__device__ __forceinline__ double warp_min_d(double v)
 {
-    const int c = blockIdx.x;
-    __shared__ double frame[9], finv[9];
-    __shared__ double red_lo[3][128], red_hi[3][128];
-    __shared__ int per_s[3];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(kCfgWarps * 32)
+k_cfg_geom(panna_system sys, double rc, CfgGeom* __restrict__ geom, int64_t* __restrict__ cfg_cells, DevStatus* st)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * kCfgWarps + (threadIdx.x >> 5);
+    if (c >= sys.n_cfg) return;
     const int64_t a0 = sys.atom_off[c], a1 = sys.atom_off[c + 1];
-    if (threadIdx.x == 0) {
-        int any = 0;
-        for (int a = 0; a < 3; ++a) { per_s[a] = sys.pbc[3 * c + a] ? 1 : 0; any |= per_s[a]; }
-        for (int k = 0; k < 9; ++k) frame[k] = any ? sys.cell[9 * c + k] : (k % 4 == 0 ? 1.0 : 0.0);
+    int per[3];
+    for (int a = 0; a < 3; ++a) per[a] = sys.pbc[3 * c + a] ? 1 : 0;
+    const bool any = per[0] || per[1] || per[2];
+    double frame[9], finv[9];
+    for (int k = 0; k < 9; ++k) frame[k] = finv[k] = (k % 4 == 0 ? 1.0 : 0.0);
+    if (any) {
+        for (int k = 0; k < 9; ++k) frame[k] = sys.cell[9 * c + k];
         const double* m = frame;
         double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6])
                    + m[2] * (m[3] * m[7] - m[4] * m[6]);
         if (!(fabs(det) > 1e-12) || !isfinite(det)) {
-            set_status(st, PANNA_ERR_BAD_INPUT, c);
+            if (lane == 0) set_status(st, PANNA_ERR_BAD_INPUT, (int)c);
             for (int k = 0; k < 9; ++k) frame[k] = (k % 4 == 0 ? 1.0 : 0.0);
-            det = 1.0;
-            per_s[0] = per_s[1] = per_s[2] = 0;
+            per[0] = per[1] = per[2] = 0;
+        } else {
+            const double id = 1.0 / det;
+            finv[0] = (m[4] * m[8] - m[5] * m[7]) * id;
+            finv[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+            finv[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+            finv[3] = (m[5] * m[6] - m[3] * m[8]) * id;
+            finv[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+            finv[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+            finv[6] = (m[3] * m[7] - m[4] * m[6]) * id;
+            finv[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+            finv[8] = (m[0] * m[4] - m[1] * m[3]) * id;
         }
-        finv[0] = (m[4] * m[8] - m[5] * m[7]) / det;
-        finv[1] = (m[2] * m[7] - m[1] * m[8]) / det;
-        finv[2] = (m[1] * m[5] - m[2] * m[4]) / det;
-        finv[3] = (m[5] * m[6] - m[3] * m[8]) / det;
-        finv[4] = (m[0] * m[8] - m[2] * m[6]) / det;
-        finv[5] = (m[2] * m[3] - m[0] * m[5]) / det;
-        finv[6] = (m[3] * m[7] - m[4] * m[6]) / det;
-        finv[7] = (m[1] * m[6] - m[0] * m[7]) / det;
-        finv[8] = (m[0] * m[4] - m[1] * m[3]) / det;
     }
-    __syncthreads();
+    // fractional bounding box (needed on non-periodic directions only)
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    const bool all_periodic = per_s[0] && per_s[1] && per_s[2];
-    for (int64_t i = a0 + threadIdx.x; i < a1 && !all_periodic; i += blockDim.x) {
-        const double* x = sys.pos + 3 * i;
-        for (int a = 0; a < 3; ++a) {
-            double s = x[0] * finv[a] + x[1] * finv[3 + a] + x[2] * finv[6 + a];
-            lo[a] = fmin(lo[a], s);
-            hi[a] = fmax(hi[a], s);
+    if (!(per[0] && per[1] && per[2])) {
+        for (int64_t i = a0 + lane; i < a1; i += 32) {
+            const double* x = sys.pos + 3 * i;
+            for (int a = 0; a < 3; ++a) {
+                double sa = x[0] * finv[a] + x[1] * finv[3 + a] + x[2] * finv[6 + a];
+                lo[a] = fmin(lo[a], sa);
+                hi[a] = fmax(hi[a], sa);
+            }
+        }
+        for (int a = 0; a < 3; ++a) { lo[a] = warp_min_d(lo[a]); hi[a] = warp_max_d(hi[a]); }
+    }
+    CfgGeom& g = geom[c];
+    // image shift table for t in [-1,1]^3, one entry per lane
+    if (lane < 27) {
+        const int t0 = lane / 9 - 1, t1 = (lane / 3) % 3 - 1, t2 = lane % 3 - 1;
+        for (int d = 0; d < 3; ++d) {
+            double S = t0 * frame[d] + t1 * frame[3 + d] + t2 * frame[6 + d];
+            float sh = (float)S;
+            g.sh_hi[lane][d] = sh;
+            g.sh_lo[lane][d] = (float)(S - (double)sh);
         }
     }
-    for (int a = 0; a < 3; ++a) { red_lo[a][threadIdx.x] = lo[a]; red_hi[a][threadIdx.x] = hi[a]; }
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o)
-            for (int a = 0; a < 3; ++a) {
-                red_lo[a][threadIdx.x] = fmin(red_lo[a][threadIdx.x], red_lo[a][threadIdx.x + o]);
-                red_hi[a][threadIdx.x] = fmax(red_hi[a][threadIdx.x], red_hi[a][threadIdx.x + o]);
-            }
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    CfgGeom g;
+    if (lane != 0) return;
     for (int k = 0; k < 9; ++k) { g.cell[k] = frame[k]; g.cinv[k] = finv[k]; }
     // perpendicular widths of the frame
     const double* A = frame; const double* B = frame + 3; const double* Cc = frame + 6;
@@ -208,22 +229,21 @@ __global__ void k_cfg_geom(panna_system sys, double rc, CfgGeom* __restrict__ ge
                    vol / sqrt(axb[0] * axb[0] + axb[1] * axb[1] + axb[2] * axb[2])};
     const double rcw = rc * (1.0 + 1e-9);   // cells strictly wider than rc
     double ext[3];
-    int64_t n_at = a1 - a0;
+    const int64_t n_at = a1 - a0;
     for (int a = 0; a < 3; ++a) {
-        g.per[a] = per_s[a];
-        if (g.per[a]) {
+        g.per[a] = per[a];
+        if (per[a]) {
             g.lo[a] = 0.0;
             ext[a] = 1.0;
         } else {
-            g.lo[a] = n_at > 0 ? red_lo[a][0] : 0.0;
-            ext[a] = n_at > 0 ? fmax(red_hi[a][0] - red_lo[a][0], 0.0) : 0.0;
+            g.lo[a] = n_at > 0 ? lo[a] : 0.0;
+            ext[a] = n_at > 0 ? fmax(hi[a] - lo[a], 0.0) : 0.0;
         }
-        double phys = ext[a] * h[a];
-        double nc = floor(phys / rcw);
+        double nc = floor(ext[a] * h[a] / rcw);
         g.n[a] = nc < 1.0 ? 1 : (nc > 1024.0 ? 1024 : (int)nc);
     }
     // no more cells than max(1, 2 * atoms): wider cells keep the search exact
-    int64_t lim = n_at > 0 ? 2 * n_at : 1;
+    const int64_t lim = n_at > 0 ? 2 * n_at : 1;
     while ((int64_t)g.n[0] * g.n[1] * g.n[2] > lim) {
         int a = 0;
         if (g.n[1] > g.n[a]) a = 1;
@@ -231,27 +251,15 @@ __global__ void k_cfg_geom(panna_system sys, double rc, CfgGeom* __restrict__ ge
         g.n[a] = (g.n[a] + 1) / 2;
     }
     for (int a = 0; a < 3; ++a) {
-        double e = ext[a] > 0.0 ? ext[a] : 1.0;
+        const double e = ext[a] > 0.0 ? ext[a] : 1.0;
         g.inv_w[a] = (double)g.n[a] / e;
-        double cw = h[a] * e / g.n[a];   // perpendicular cell width
+        const double cw = h[a] * e / g.n[a];   // perpendicular cell width
         int K = 1;
-        if (g.per[a] && cw < rcw) K = (int)ceil(rcw / cw);
+        if (per[a] && cw < rcw) K = (int)ceil(rcw / cw);
         g.K[a] = K;
     }
     g.ncells = g.n[0] * g.n[1] * g.n[2];
     g.cell_base = 0;
-    for (int t0 = -1; t0 <= 1; ++t0)
-        for (int t1 = -1; t1 <= 1; ++t1)
-            for (int t2 = -1; t2 <= 1; ++t2) {
-                int k = (t0 + 1) * 9 + (t1 + 1) * 3 + (t2 + 1);
-                for (int d = 0; d < 3; ++d) {
-                    double S = t0 * frame[d] + t1 * frame[3 + d] + t2 * frame[6 + d];
-                    float sh = (float)S;
-                    g.sh_hi[k][d] = sh;
-                    g.sh_lo[k][d] = (float)(S - (double)sh);
-                }
-            }
-    geom[c] = g;
     cfg_cells[c] = g.ncells;
 }
 
@@ -524,7 +532,8 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
     unsigned nbA = (unsigned)((N + 255) / 256);
     if (nbA == 0) nbA = 1;
     k_atom_cfg<<<nbA, 256, 0, s>>>(sys.atom_off, C, N, w.atom_cfg);
-    k_cfg_geom<<<(unsigned)C, 128, 0, s>>>(sys, d.rc_d, w.geom, w.cell_count, w.status);
+    k_cfg_geom<<<(unsigned)((C + kCfgWarps - 1) / kCfgWarps), kCfgWarps * 32, 0, s>>>(sys, d.rc_d, w.geom,
+                                                                                      w.cell_count, w.status);
     *launches += 2;
     // cell bases: scan of per-config cell counts (stored temporarily in cell_count[0..C))
     e = exclusive_scan_i64(w.cell_count, w.cell_start, C, w.scan_tmp, s, launches);

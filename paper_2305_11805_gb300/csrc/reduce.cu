@@ -23,19 +23,26 @@ __device__ __forceinline__ double block_sum_d(double v)
     return t;   // valid in thread 0
 }
 
-// partial sums over chunk b of configuration c
-__global__ void k_cfg_partial(const int64_t* __restrict__ atom_off, int B, const int32_t* __restrict__ row_of_atom,
-                              const float* __restrict__ E_rows, const float* __restrict__ vir_atom,
-                              float* __restrict__ E_atom, double* __restrict__ part)
+// partial sums over chunk b of configuration c: one warp per (configuration, chunk)
+constexpr int kCfgRedWarps = 8;
+
+__global__ void __launch_bounds__(kCfgRedWarps * 32)
+k_cfg_partial(int64_t C, const int64_t* __restrict__ atom_off, int B, const int32_t* __restrict__ row_of_atom,
+              const float* __restrict__ E_rows, const float* __restrict__ vir_atom, float* __restrict__ E_atom,
+              double* __restrict__ part)
 {
-    const int c = blockIdx.x, b = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * kCfgRedWarps + (threadIdx.x >> 5);
+    if (gw >= C * B) return;
+    const int64_t c = gw / B;
+    const int b = (int)(gw % B);
     const int64_t a0 = atom_off[c], a1 = atom_off[c + 1];
     const int64_t per = (a1 - a0 + B - 1) / B;
     const int64_t s0 = a0 + b * per, s1 = min(a1, s0 + per);
     double v[kCfgVals];
 #pragma unroll
     for (int k = 0; k < kCfgVals; ++k) v[k] = 0.0;
-    for (int64_t i = s0 + threadIdx.x; i < s1; i += kRedThreads) {
+    for (int64_t i = s0 + lane; i < s1; i += 32) {
         const float e = E_rows[row_of_atom[i]];
         if (E_atom) E_atom[i] = e;
         v[0] += e;
@@ -43,11 +50,14 @@ __global__ void k_cfg_partial(const int64_t* __restrict__ atom_off, int B, const
 #pragma unroll
             for (int k = 0; k < 9; ++k) v[1 + k] += vir_atom[9 * i + k];
     }
-    double* out = part + ((size_t)c * B + b) * kCfgVals;
 #pragma unroll
-    for (int k = 0; k < kCfgVals; ++k) {
-        double t = block_sum_d(v[k]);
-        if (threadIdx.x == 0) out[k] = t;
+    for (int k = 0; k < kCfgVals; ++k)
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0) {
+        double* out = part + ((size_t)c * B + b) * kCfgVals;
+#pragma unroll
+        for (int k = 0; k < kCfgVals; ++k) out[k] = v[k];
     }
 }
 
@@ -67,16 +77,16 @@ __global__ void k_cfg_final(int64_t C, int B, const double* __restrict__ part, d
 
 int cfg_chunks(int64_t N, int64_t C)
 {
-    int64_t B = N / (C * 4096) + 1;
-    return (int)(B > 256 ? 256 : B);
+    int64_t B = N / (C * 1024) + 1;
+    return (int)(B > 4096 ? 4096 : B);
 }
 
 cudaError_t launch_cfg_reduce(const Work& w, const float* E_rows, const float* vir_atom, double* E_cfg, double* virial,
                               float* E_atom, double* part, cudaStream_t s, int* launches)
 {
     const int B = cfg_chunks(w.N, w.C);
-    k_cfg_partial<<<dim3((unsigned)w.C, (unsigned)B), kRedThreads, 0, s>>>(w.sys->atom_off, B, w.row_of_atom, E_rows,
-                                                                           vir_atom, E_atom, part);
+    k_cfg_partial<<<(unsigned)((w.C * B + kCfgRedWarps - 1) / kCfgRedWarps), kCfgRedWarps * 32, 0, s>>>(
+        w.C, w.sys->atom_off, B, w.row_of_atom, E_rows, vir_atom, E_atom, part);
     k_cfg_final<<<(unsigned)((w.C + 127) / 128), 128, 0, s>>>(w.C, B, part, E_cfg, virial);
     *launches += 2;
     return cudaGetLastError();
@@ -111,10 +121,15 @@ __global__ void k_loss_partial(int64_t C, int64_t N, const double* __restrict__ 
 
 __global__ void k_loss_final(int64_t C, int64_t N, double w_force, const double* __restrict__ part, double* __restrict__ loss)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
     double le = 0.0, lf = 0.0;
-    for (int b = 0; b < kLossBlocks; ++b) { le += part[2 * b]; lf += part[2 * b + 1]; }
-    *loss = le / (double)C + w_force * lf / (3.0 * (double)N);
+    for (int b = lane; b < kLossBlocks; b += 32) { le += part[2 * b]; lf += part[2 * b + 1]; }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        le += __shfl_xor_sync(0xffffffffu, le, o);
+        lf += __shfl_xor_sync(0xffffffffu, lf, o);
+    }
+    if (lane == 0 && blockIdx.x == 0) *loss = le / (double)C + w_force * lf / (3.0 * (double)N);
 }
 
 cudaError_t launch_loss(const Work& w, const double* E_cfg, const double* E_ref, const float* F, const float* F_ref,

@@ -1,0 +1,62 @@
+"""The torch.autograd.Function around the C ABI: a loss written in torch over (E, F)
+back-propagates to the network parameters through the hand-written double backward, and
+matches the FP64 oracle's gradient of the same loss."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2305_11805_gb300 import panna as P
+from paper_2305_11805_gb300 import workloads as W
+from tests import gpu_common as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_11805_gb300 import build
+    build.build()
+    return torch
+
+
+def test_autograd_energy_force_loss_gradient(torch_cuda):
+    torch = torch_cuda
+    from paper_2305_11805_gb300.autograd import energy_forces
+    wl = W.make("molecules16")
+    pot = P.Potential(wl.desc, wl.archs)
+    sysd = P.DeviceSystem(wl.system)
+    th32 = wl.theta.astype(np.float32)
+    theta = torch.tensor(th32, device="cuda", requires_grad=True)
+    E_ref = torch.as_tensor(wl.e_ref, dtype=torch.float64, device="cuda")
+    F_ref = torch.as_tensor(wl.f_ref, dtype=torch.float32, device="cuda")
+    E, F = energy_forces(theta, pot, sysd)
+    loss = ((E - E_ref) ** 2).mean() + wl.w_force * ((F.double() - F_ref.double()) ** 2).mean()
+    loss.backward()
+    ref = O.batch(wl.system, wl.desc, wl.archs, th32.astype(np.float64), e_ref=wl.e_ref,
+                  f_ref=wl.f_ref.astype(np.float32).astype(np.float64), w_force=wl.w_force, param_grad=True)
+    assert abs(loss.item() - ref["loss"]) <= 1e-5 * abs(ref["loss"])
+    errs = H.layer_errors(wl.archs, theta.grad.cpu().numpy().astype(np.float64), ref["dtheta"])
+    assert max(errs) <= H.TOL_DTHETA, errs
+
+
+def test_autograd_energy_only_and_force_only(torch_cuda):
+    torch = torch_cuda
+    from paper_2305_11805_gb300.autograd import energy_forces
+    wl = W.make("ragged8")
+    pot = P.Potential(wl.desc, wl.archs)
+    sysd = P.DeviceSystem(wl.system)
+    theta = torch.tensor(wl.theta.astype(np.float32), device="cuda", requires_grad=True)
+    E, F = energy_forces(theta, pot, sysd)
+    E.sum().backward()
+    gE = theta.grad.clone()
+    theta.grad = None
+    E, F = energy_forces(theta, pot, sysd)
+    (F ** 2).sum().backward()
+    gF = theta.grad.clone()
+    theta.grad = None
+    E, F = energy_forces(theta, pot, sysd)
+    (E.sum() + (F ** 2).sum()).backward()
+    assert torch.allclose(theta.grad, gE + gF, rtol=1e-5, atol=1e-6 * float(theta.grad.abs().max()))
