@@ -55,8 +55,17 @@ typedef enum {
 /* Activation codes (Sec. II.A: Gaussian, ReLU, tanh; linear for the output). */
 enum { PANNA_ACT_LINEAR = 0, PANNA_ACT_GAUSSIAN = 1, PANNA_ACT_RELU = 2, PANNA_ACT_TANH = 3 };
 
-/* Network precision. */
-enum { PANNA_MLP_FP32 = 0, PANNA_MLP_BF16 = 1 };
+/*
+ * Network precision.
+ *   PANNA_MLP_FP32       FP32 CUDA-core GEMMs.
+ *   PANNA_MLP_BF16       tensor cores (tcgen05), BF16 operands with FP32 accumulation; every
+ *                        operand is carried as a pair of BF16 numbers (hi + lo) and each
+ *                        product takes three BF16 MMAs (hi*hi + hi*lo + lo*hi): about 16
+ *                        significant bits per operand.
+ *   PANNA_MLP_BF16_FAST  tensor cores, one BF16 rounding per operand (8 significant bits).
+ * With either BF16 mode the descriptor and adjoint stay in FP32.
+ */
+enum { PANNA_MLP_FP32 = 0, PANNA_MLP_BF16 = 1, PANNA_MLP_BF16_FAST = 2 };
 
 /*
  * Descriptor parameters (host memory; copied by panna_create).
@@ -164,7 +173,8 @@ panna_status panna_set_async(panna_ctx* ctx, int32_t async);
 
 /*
  * Arithmetic of the angular descriptor terms (descriptor, adjoint, JVP):
- *   0 = automatic (default): extended precision with FP32 networks, plain FP32 with BF16;
+ *   0 = automatic (default): extended precision unless the network runs in
+ *       PANNA_MLP_BF16_FAST, whose own error dominates;
  *   1 = extended: unit vectors, cos/sin of the angle and (1 + cos(theta - theta_m))/2
  *       carried as pairs of floats (about 4x smaller error under the zeta-th power,
  *       about twice the arithmetic);
@@ -201,7 +211,8 @@ panna_status panna_descriptors(panna_ctx* ctx, const panna_system* sys, float* G
  *   F      [n_atoms*3] FP32 forces -dE/dx (device, required)
  *   virial [n_cfg*9] FP64, W_ab = -sum over neighbour entries q_a r_b with
  *          q = dE_i/dr_ij (device, may be NULL)
- * mlp_precision: PANNA_MLP_FP32 or PANNA_MLP_BF16 (BF16 operands, FP32 accumulation).
+ * mlp_precision: PANNA_MLP_FP32, PANNA_MLP_BF16 or PANNA_MLP_BF16_FAST (see above); the BF16
+ * modes need at least one hidden layer and a descriptor size that is a multiple of 8.
  */
 panna_status panna_energy_forces(panna_ctx* ctx, const panna_system* sys, const float* theta,
                                  int32_t mlp_precision, double* E_cfg, float* E_atom, float* F,

@@ -105,11 +105,12 @@ struct Layout {
     float* alpha_rows = nullptr;
     float* wdot = nullptr;
     double* loss_part = nullptr;
+    void* tc_ws = nullptr;   // BF16 tensor-core network buffers
 };
 
 constexpr int kSplits = 16;
 
-void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, Layout& L)
+void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, Layout& L)
 {
     const int S = c->d.S, D = c->d.D, cap = c->cap;
     const MlpPlan& p = c->plan;
@@ -154,6 +155,7 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, Layout& L)
     b.seg_off = w.seg_off;
     b.tile_start = a.take<int32_t>(S + 1);
     b.splits = kSplits;
+    if (bf16) L.tc_ws = a.take<char>(tc_workspace_bytes(p, N, true));
     if (train) {
         for (int l = 1; l <= p.L; ++l) {
             b.Zd[l] = a.take<float>((size_t)N * p.ld[l]);
@@ -171,12 +173,12 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, Layout& L)
     }
 }
 
-panna_status prepare(panna_ctx* c, const panna_system* sys, bool train, Layout& L, cudaStream_t s)
+panna_status prepare(panna_ctx* c, const panna_system* sys, bool train, bool bf16, Layout& L, cudaStream_t s)
 {
     const int64_t N = sys->n_atoms, C = sys->n_cfg;
     Arena sz;
     sz.sizing = true;
-    carve(c, sz, N, C, train, L);
+    carve(c, sz, N, C, train, bf16, L);
     if (sz.off > c->ws.cap) {
         if (c->ws.base) {
             CU(cudaStreamSynchronize(s));
@@ -195,7 +197,7 @@ panna_status prepare(panna_ctx* c, const panna_system* sys, bool train, Layout& 
     Arena real = c->ws;
     real.sizing = false;
     real.off = 0;
-    carve(c, real, N, C, train, L);
+    carve(c, real, N, C, train, bf16, L);
     L.w.sys = sys;
     return PANNA_OK;
 }
@@ -278,7 +280,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     const bool grad = rq.train || rq.vjp;
     // FP32 networks get the extended-precision angular terms (force tolerance 1e-5 of RMS);
     // BF16 networks (tolerance 1e-2) the plain FP32 form
-    const bool acc = c->ang_mode == 1 || (c->ang_mode == 0 && rq.prec == PANNA_MLP_FP32);
+    const bool acc = c->ang_mode == 1 || (c->ang_mode == 0 && rq.prec != PANNA_MLP_BF16_FAST);
     for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
     c->n_marked = 0;
     CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
@@ -295,13 +297,20 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     stage_mark(c, 1, s);
     CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl));
     stage_mark(c, 2, s);
-    CU(mlp_forward(c->plan, L.mb, rq.theta, N, s, &nl));
-    CU(mlp_energy_rows(c->plan, L.mb, N, L.E_rows, s, &nl));
     float* F = rq.F ? rq.F : L.F_int;
     double* E_cfg = rq.E_cfg ? rq.E_cfg : L.E_cfg_int;
     const bool need_forces = rq.forces || rq.train;
+    const bool tc = rq.prec == PANNA_MLP_BF16 || rq.prec == PANNA_MLP_BF16_FAST;
+    if (tc) {
+        // BF16 operands on the tensor cores: energies and dE/dG together
+        CU(mlp_bf16_energy_grad(c->plan, L.mb, rq.theta, N, L.tc_ws, rq.prec == PANNA_MLP_BF16, L.E_rows, L.g,
+                                L.w.status, s, &nl));
+    } else {
+        CU(mlp_forward(c->plan, L.mb, rq.theta, N, s, &nl));
+        CU(mlp_energy_rows(c->plan, L.mb, N, L.E_rows, s, &nl));
+    }
     if (need_forces) {
-        CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl));
+        if (!tc) CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl));
         stage_mark(c, 3, s);
         CU(cudaMemsetAsync(F, 0, sizeof(float) * 3 * N, s));
         CU(launch_adjoint(L.w, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, acc, s, &nl));
@@ -342,7 +351,7 @@ panna_status run(panna_ctx* c, const panna_system* sys, const Request& rq, cudaS
     const bool train = rq.train || rq.vjp;
     for (int attempt = 0; attempt < 2; ++attempt) {
         Layout L;
-        ST(prepare(c, sys, train, L, s));
+        ST(prepare(c, sys, train, rq.prec != PANNA_MLP_FP32, L, s));
         c->last_launches = 0;
         ST(run_once(c, sys, rq, L, s));
         CU(cudaGetLastError());
@@ -521,7 +530,7 @@ panna_status panna_neighbors(panna_ctx* c, const panna_system* sys, int64_t cap_
     CU(cudaSetDevice(c->device));
     for (int attempt = 0; attempt < 2; ++attempt) {
         Layout L;
-        ST(prepare(c, sys, false, L, s));
+        ST(prepare(c, sys, false, false, L, s));
         c->last_launches = 0;
         CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
         CU(build_neighbors(L.w, c->d, s, &c->last_launches));
@@ -555,8 +564,12 @@ panna_status panna_energy_forces(panna_ctx* c, const panna_system* sys, const fl
                                  double* E_cfg, float* E_atom, float* F, double* virial, panna_stream_t stream)
 {
     if (!theta || !E_cfg || !F) return fail(PANNA_ERR_INVALID_ARG, "theta, E_cfg and F are required");
-    if (prec != PANNA_MLP_FP32 && prec != PANNA_MLP_BF16) return fail(PANNA_ERR_INVALID_ARG, "bad precision");
-    if (prec == PANNA_MLP_BF16) return fail(PANNA_ERR_UNSUPPORTED, "BF16 networks are not available yet");
+    if (prec != PANNA_MLP_FP32 && prec != PANNA_MLP_BF16 && prec != PANNA_MLP_BF16_FAST)
+        return fail(PANNA_ERR_INVALID_ARG, "bad precision");
+    if (prec != PANNA_MLP_FP32 && c && c->plan.L < 2)
+        return fail(PANNA_ERR_UNSUPPORTED, "BF16 networks need at least one hidden layer");
+    if (prec != PANNA_MLP_FP32 && c && (c->d.D % 8 != 0))
+        return fail(PANNA_ERR_UNSUPPORTED, "BF16 networks need a descriptor size that is a multiple of 8");
     Request rq;
     rq.theta = theta; rq.prec = prec; rq.E_cfg = E_cfg; rq.E_atom = E_atom; rq.F = F; rq.virial = virial;
     rq.forces = true; rq.energy = true;

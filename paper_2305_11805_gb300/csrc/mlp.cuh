@@ -46,6 +46,11 @@ cudaError_t mlp_forward(const MlpPlan& p, const MlpBuffers& b, const float* thet
 cudaError_t mlp_energy_rows(const MlpPlan& p, const MlpBuffers& b, int64_t N, float* E_rows, cudaStream_t s, int* launches);
 cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, float* g,
                            cudaStream_t s, int* launches);
+// BF16 tensor-core networks (mlp_tc.cu): energies and input gradients; ws from tc_workspace_bytes
+size_t tc_workspace_bytes(const MlpPlan& p, int64_t N, bool split);
+cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, void* ws,
+                                 bool split, float* E_rows, float* g, DevStatus* status, cudaStream_t s,
+                                 int* launches);
 cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, const float* wdot,
                            const float* alpha_rows, float* dtheta, cudaStream_t s, int* launches);
 

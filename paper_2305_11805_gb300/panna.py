@@ -22,7 +22,7 @@ MAX_LAYERS = 8
 
 PANNA_OK, PANNA_ERR_INVALID_ARG, PANNA_ERR_UNSUPPORTED, PANNA_ERR_NEIGHBOR_OVERFLOW = 0, 1, 2, 3
 PANNA_ERR_TIMEOUT, PANNA_ERR_CUDA, PANNA_ERR_NO_MEMORY, PANNA_ERR_BAD_INPUT = 4, 5, 6, 7
-PANNA_MLP_FP32, PANNA_MLP_BF16 = 0, 1
+PANNA_MLP_FP32, PANNA_MLP_BF16, PANNA_MLP_BF16_FAST = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
