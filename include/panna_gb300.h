@@ -173,14 +173,24 @@ panna_status panna_set_async(panna_ctx* ctx, int32_t async);
 
 /*
  * Arithmetic of the angular descriptor terms (descriptor, adjoint, JVP):
- *   0 = automatic (default): extended precision unless the network runs in
- *       PANNA_MLP_BF16_FAST, whose own error dominates;
+ *   0 = automatic (default): extended precision with FP32 networks (force tolerance 1e-5 of
+ *       RMS), plain FP32 with the BF16 modes (their tolerance is 1e-2);
  *   1 = extended: unit vectors, cos/sin of the angle and (1 + cos(theta - theta_m))/2
  *       carried as pairs of floats (about 4x smaller error under the zeta-th power,
  *       about twice the arithmetic);
  *   2 = plain FP32.
  */
 panna_status panna_set_angular_precision(panna_ctx* ctx, int32_t mode);
+
+/*
+ * Kernel variants and the autotuner.  knob "autotune": 1 (default) = on the first
+ * synchronous call for a given problem signature (atoms, configurations, neighbour
+ * capacity, precision) time the candidate variants on the caller's stream and keep the
+ * fastest; 0 = use a fixed rule.  knob "adjoint": -1 (default) = tuned, 0 = pairs by
+ * species block (8 warps per CTA), 1 = all pairs of an atom in one flattened range (4 warps
+ * per CTA).  Returns PANNA_ERR_INVALID_ARG for an unknown knob or value.
+ */
+panna_status panna_set_tuning(panna_ctx* ctx, const char* knob, int32_t value);
 
 /* Synchronise `stream` and return (and clear) the device status word. */
 panna_status panna_check(panna_ctx* ctx, panna_stream_t stream);
@@ -243,6 +253,21 @@ panna_status panna_loss_grad(panna_ctx* ctx, const panna_system* sys, const floa
                              const double* E_ref, const float* F_ref, double w_force,
                              double* loss, float* dtheta, double* E_cfg, float* F,
                              panna_stream_t stream);
+
+/*
+ * CUDA-graph form of panna_energy_forces for repeated evaluation of one ragged batch (the
+ * same device arrays, contents updated in place, e.g. positions in an MD loop):
+ * panna_capture runs the call once synchronously (sizing the workspace, tuning kernel
+ * variants, checking the status word), then records the same sequence of kernel launches
+ * into a CUDA graph owned by the context (on `stream`, or on an internal stream when
+ * `stream` is the legacy default stream).  panna_replay launches that graph on `stream`
+ * without any host synchronisation; call panna_check afterwards to read the device status
+ * word (a neighbour-capacity overflow inside a replay is reported there, not retried).
+ * The graph keeps the pointers given to panna_capture; a new capture replaces the old one.
+ */
+panna_status panna_capture(panna_ctx* ctx, const panna_system* sys, const float* theta, int32_t mlp_precision,
+                           double* E_cfg, float* E_atom, float* F, double* virial, panna_stream_t stream);
+panna_status panna_replay(panna_ctx* ctx, panna_stream_t stream);
 
 /*
  * Number of kernels the last compute call launched (for launch accounting), and the

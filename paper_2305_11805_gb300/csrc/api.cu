@@ -75,7 +75,18 @@ struct panna_ctx {
     int async = 0;
     int profiling = 0;
     int ang_mode = 0;
+    int autotune = 1;
+    int force_adjoint = -1;
     int last_launches = 0;
+    // autotuner: kernel variant per problem signature, measured on the first call
+    struct Tuned { int64_t N, C; int cap, prec, adjoint; };
+    Tuned tuned[16];
+    int n_tuned = 0;
+    cudaEvent_t tev[3] = {};
+    // captured graph
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    int graph_launches = 0;
     Arena ws;
     DevStatus* h_status = nullptr;   // pinned
     cudaEvent_t ev[kNumStages + 1] = {};
@@ -98,6 +109,7 @@ struct Layout {
     float* vir_atom = nullptr;
     double* cfg_part = nullptr;
     float* F_int = nullptr;
+    float* F_tune = nullptr;
     double* E_cfg_int = nullptr;
     // training
     float* u = nullptr;
@@ -143,6 +155,7 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, 
     L.vir_atom = a.take<float>(9 * (size_t)N);
     L.cfg_part = a.take<double>((size_t)C * cfg_chunks(N, C) * 10);
     L.F_int = a.take<float>(3 * (size_t)N);
+    L.F_tune = a.take<float>(3 * (size_t)N);
     L.E_cfg_int = a.take<double>(C);
     MlpBuffers& b = L.mb;
     b.G = L.G;
@@ -273,6 +286,33 @@ struct Request {
     float* dtheta = nullptr;
 };
 
+// Adjoint variant for this problem signature: measured once (both variants into scratch
+// forces, CUDA events on the caller's stream), then cached.  Asynchronous calls never
+// measure (they may be under stream capture) and use the cached or default choice.
+int tuned_adjoint(panna_ctx* c, const panna_system* sys, int prec, const Layout& L, bool acc, cudaStream_t s)
+{
+    if (c->force_adjoint >= 0) return c->force_adjoint;
+    for (int k = 0; k < c->n_tuned; ++k) {
+        const panna_ctx::Tuned& t = c->tuned[k];
+        if (t.N == sys->n_atoms && t.C == sys->n_cfg && t.cap == c->cap && t.prec == prec) return t.adjoint;
+    }
+    const int fallback = c->d.S > 1 ? 1 : 0;
+    if (!c->autotune || c->async || sys->n_atoms == 0) return fallback;
+    float ms[2] = {0.f, 0.f};
+    int dummy = 0;
+    for (int v = 0; v < 2; ++v) {
+        cudaEventRecord(c->tev[0], s);
+        launch_adjoint(L.w, c->d, L.g, L.F_tune, nullptr, acc, v, s, &dummy);
+        cudaEventRecord(c->tev[1], s);
+        cudaEventSynchronize(c->tev[1]);
+        cudaEventElapsedTime(&ms[v], c->tev[0], c->tev[1]);
+    }
+    const int best = ms[1] < ms[0] ? 1 : 0;
+    panna_ctx::Tuned t{sys->n_atoms, sys->n_cfg, c->cap, prec, best};
+    c->tuned[c->n_tuned < 16 ? c->n_tuned++ : 15] = t;
+    return best;
+}
+
 panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, Layout& L, cudaStream_t s)
 {
     int& nl = c->last_launches;
@@ -280,7 +320,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     const bool grad = rq.train || rq.vjp;
     // FP32 networks get the extended-precision angular terms (force tolerance 1e-5 of RMS);
     // BF16 networks (tolerance 1e-2) the plain FP32 form
-    const bool acc = c->ang_mode == 1 || (c->ang_mode == 0 && rq.prec != PANNA_MLP_BF16_FAST);
+    const bool acc = c->ang_mode == 1 || (c->ang_mode == 0 && rq.prec == PANNA_MLP_FP32);
     for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
     c->n_marked = 0;
     CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
@@ -312,8 +352,9 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     if (need_forces) {
         if (!tc) CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl));
         stage_mark(c, 3, s);
+        const int variant = tuned_adjoint(c, sys, rq.prec, L, acc, s);
         CU(cudaMemsetAsync(F, 0, sizeof(float) * 3 * N, s));
-        CU(launch_adjoint(L.w, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, acc, s, &nl));
+        CU(launch_adjoint(L.w, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, acc, variant, s, &nl));
     }
     stage_mark(c, 4, s);
     CU(launch_cfg_reduce(L.w, L.E_rows, (rq.virial && need_forces) ? L.vir_atom : nullptr, E_cfg, rq.virial,
@@ -464,6 +505,7 @@ panna_status panna_create(const panna_desc_params* p, int32_t n_archs, const pan
         return fail(PANNA_ERR_CUDA, "pinned status allocation failed");
     }
     for (int k = 0; k <= kNumStages; ++k) cudaEventCreate(&c->ev[k]);
+    for (int k = 0; k < 3; ++k) cudaEventCreate(&c->tev[k]);
     *out = c;
     return PANNA_OK;
 }
@@ -475,6 +517,10 @@ void panna_destroy(panna_ctx* c)
     if (c->h_status) cudaFreeHost(c->h_status);
     for (int k = 0; k <= kNumStages; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    for (int k = 0; k < 3; ++k)
+        if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
 }
 
@@ -501,6 +547,21 @@ panna_status panna_set_angular_precision(panna_ctx* c, int32_t mode)
     if (!c || mode < 0 || mode > 2) return fail(PANNA_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
     c->ang_mode = mode;
     return PANNA_OK;
+}
+
+panna_status panna_set_tuning(panna_ctx* c, const char* knob, int32_t value)
+{
+    if (!c || !knob) return fail(PANNA_ERR_INVALID_ARG, "null argument");
+    if (strcmp(knob, "autotune") == 0 && (value == 0 || value == 1)) {
+        c->autotune = value;
+        c->n_tuned = 0;
+        return PANNA_OK;
+    }
+    if (strcmp(knob, "adjoint") == 0 && value >= -1 && value <= 1) {
+        c->force_adjoint = value;
+        return PANNA_OK;
+    }
+    return fail(PANNA_ERR_INVALID_ARG, "unknown tuning knob or value: %s=%d", knob, value);
 }
 
 panna_status panna_check(panna_ctx* c, panna_stream_t stream)
@@ -595,6 +656,60 @@ panna_status panna_loss_grad(panna_ctx* c, const panna_system* sys, const float*
     rq.theta = theta; rq.train = true; rq.E_ref = E_ref; rq.F_ref = F_ref; rq.w_force = w_force; rq.loss = loss;
     rq.dtheta = dtheta; rq.E_cfg = E_cfg; rq.F = F; rq.forces = true; rq.energy = true;
     return run(c, sys, rq, (cudaStream_t)stream);
+}
+
+panna_status panna_capture(panna_ctx* c, const panna_system* sys, const float* theta, int32_t prec, double* E_cfg,
+                           float* E_atom, float* F, double* virial, panna_stream_t stream)
+{
+    if (!c) return fail(PANNA_ERR_INVALID_ARG, "null context");
+    // 1. one synchronous call: workspace sized, variants tuned, inputs validated
+    ST(panna_energy_forces(c, sys, theta, prec, E_cfg, E_atom, F, virial, stream));
+    // 2. record the same launches
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) {
+        if (!c->capture_stream) CU(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+        s = c->capture_stream;
+    }
+    if (c->graph_exec) {
+        CU(cudaGraphExecDestroy(c->graph_exec));
+        c->graph_exec = nullptr;
+    }
+    Request rq;
+    rq.theta = theta; rq.prec = prec; rq.E_cfg = E_cfg; rq.E_atom = E_atom; rq.F = F; rq.virial = virial;
+    rq.forces = true; rq.energy = true;
+    const int old_async = c->async, old_prof = c->profiling;
+    c->async = 1;
+    c->profiling = 0;
+    Layout L;
+    panna_status st = prepare(c, sys, false, prec != PANNA_MLP_FP32, L, s);
+    cudaGraph_t g = nullptr;
+    if (st == PANNA_OK) {
+        CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        c->last_launches = 0;
+        st = run_once(c, sys, rq, L, s);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st == PANNA_OK && e != cudaSuccess)
+            st = fail(PANNA_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+    }
+    c->async = old_async;
+    c->profiling = old_prof;
+    if (st != PANNA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    cudaError_t e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(PANNA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    c->graph_launches = c->last_launches;
+    return PANNA_OK;
+}
+
+panna_status panna_replay(panna_ctx* c, panna_stream_t stream)
+{
+    if (!c || !c->graph_exec) return fail(PANNA_ERR_INVALID_ARG, "no captured graph");
+    CU(cudaGraphLaunch(c->graph_exec, (cudaStream_t)stream));
+    c->last_launches = c->graph_launches;
+    return PANNA_OK;
 }
 
 int32_t panna_last_launch_count(const panna_ctx* c) { return c ? c->last_launches : -1; }

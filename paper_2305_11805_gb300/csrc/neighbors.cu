@@ -353,6 +353,26 @@ __device__ __forceinline__ float dd_rel(float xjh, float xjl, float sh, float sl
 
 constexpr int kNbWarps = 8;
 
+// Rare paths with FP64 arithmetic, kept out of line: GB300 runs FP64 at 1/64 of the FP32
+// rate, and the hot loop must not carry (even predicated-off) FP64 instructions.
+__device__ __noinline__ void shift_hilo(const CfgGeom& g, int t0, int t1, int t2, float* shh, float* shl)
+{
+    for (int d = 0; d < 3; ++d) {
+        double Sv = t0 * g.cell[d] + t1 * g.cell[3 + d] + t2 * g.cell[6 + d];
+        shh[d] = (float)Sv;
+        shl[d] = (float)(Sv - (double)shh[d]);
+    }
+}
+
+__device__ __noinline__ bool retest_fp64(float4 xjh, float4 xjl, const float* shh, const float* shl, float4 xih,
+                                         float4 xil, double rc2d)
+{
+    double rx = ((double)xjh.x + (double)xjl.x) + ((double)shh[0] + (double)shl[0]) - ((double)xih.x + (double)xil.x);
+    double ry = ((double)xjh.y + (double)xjl.y) + ((double)shh[1] + (double)shl[1]) - ((double)xih.y + (double)xil.y);
+    double rz = ((double)xjh.z + (double)xjl.z) + ((double)shh[2] + (double)shl[2]) - ((double)xih.z + (double)xil.z);
+    return (rx * rx + ry * ry + rz * rz) < rc2d;
+}
+
 __global__ void __launch_bounds__(kNbWarps * 32)
 k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__ geom,
             const int32_t* __restrict__ atom_cfg, const int32_t* __restrict__ atom_cell,
@@ -396,11 +416,7 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
                     int k = (t0 + 1) * 9 + (t1 + 1) * 3 + (t2 + 1);
                     for (int d = 0; d < 3; ++d) { shh[d] = g.sh_hi[k][d]; shl[d] = g.sh_lo[k][d]; }
                 } else {
-                    for (int d = 0; d < 3; ++d) {
-                        double Sv = t0 * g.cell[d] + t1 * g.cell[3 + d] + t2 * g.cell[6 + d];
-                        shh[d] = (float)Sv;
-                        shl[d] = (float)(Sv - (double)shh[d]);
-                    }
+                    shift_hilo(g, t0, t1, t2, shh, shl);
                 }
                 const bool self_image = (t0 == 0 && t1 == 0 && t2 == 0);
                 const int64_t gc = g.cell_base + (c0 * n1 + c1) * n2 + c2;
@@ -425,14 +441,7 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
                             dz = dd_rel(xjh.z, xjl.z, shh[2], shl[2], xih.z, xil.z);
                             r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
                             if (fabsf(r2 - rc2) <= 2e-6f * rc2) {
-                                // FP64 re-test near the cutoff
-                                double rx = ((double)xjh.x + (double)xjl.x) + ((double)shh[0] + (double)shl[0])
-                                          - ((double)xih.x + (double)xil.x);
-                                double ry = ((double)xjh.y + (double)xjl.y) + ((double)shh[1] + (double)shl[1])
-                                          - ((double)xih.y + (double)xil.y);
-                                double rz = ((double)xjh.z + (double)xjl.z) + ((double)shh[2] + (double)shl[2])
-                                          - ((double)xih.z + (double)xil.z);
-                                in = (rx * rx + ry * ry + rz * rz) < rc2d;
+                                in = retest_fp64(xjh, xjl, shh, shl, xih, xil, rc2d);   // FP64 near the cutoff
                             } else {
                                 in = r2 < rc2;
                             }

@@ -77,8 +77,8 @@ __global__ void k_cfg_final(int64_t C, int B, const double* __restrict__ part, d
 
 int cfg_chunks(int64_t N, int64_t C)
 {
-    int64_t B = N / (C * 1024) + 1;
-    return (int)(B > 4096 ? 4096 : B);
+    int64_t B = N / (C * 256) + 1;
+    return (int)(B > 8192 ? 8192 : B);
 }
 
 cudaError_t launch_cfg_reduce(const Work& w, const float* E_rows, const float* vir_atom, double* E_cfg, double* virial,

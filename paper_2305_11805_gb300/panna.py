@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
         "panna_set_async": (i32, [_vp, i32]),
         "panna_check": (i32, [_vp, _vp]),
         "panna_set_angular_precision": (i32, [_vp, i32]),
+        "panna_set_tuning": (i32, [_vp, C.c_char_p, i32]),
         "panna_neighbors": (i32, [_vp, C.POINTER(panna_system), i64, _vp, _vp, _vp, C.POINTER(i64), _vp]),
         "panna_descriptors": (i32, [_vp, C.POINTER(panna_system), _vp, _vp]),
         "panna_energy_forces": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
@@ -86,6 +87,8 @@ def load(path: str = LIB_PATH):
         "panna_set_profiling": (i32, [_vp, i32]),
         "panna_stage_ms": (f32, [_vp, C.c_char_p]),
         "panna_descriptors_static": (i32, [C.POINTER(panna_desc_params), C.POINTER(panna_system), _vp, _vp]),
+        "panna_capture": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
+        "panna_replay": (i32, [_vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -98,9 +101,9 @@ def load(path: str = LIB_PATH):
 def exported_symbols() -> Sequence[str]:
     return ["panna_version", "panna_last_error", "panna_descriptor_size", "panna_create", "panna_destroy",
             "panna_param_count", "panna_set_neighbor_capacity", "panna_neighbor_capacity", "panna_set_async",
-            "panna_check", "panna_set_angular_precision", "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
+            "panna_check", "panna_set_angular_precision", "panna_set_tuning", "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
-            "panna_descriptors_static"]
+            "panna_descriptors_static", "panna_capture", "panna_replay"]
 
 
 def _check(status: int):
@@ -177,6 +180,10 @@ def panna_set_angular_precision(ctx: int, mode: int):
     _check(load().panna_set_angular_precision(ctx, int(mode)))
 
 
+def panna_set_tuning(ctx: int, knob: str, value: int):
+    _check(load().panna_set_tuning(ctx, knob.encode(), int(value)))
+
+
 def panna_check(ctx: int, stream=None):
     _check(load().panna_check(ctx, _stream(stream)))
 
@@ -224,6 +231,15 @@ def panna_descriptors_static(desc, sysd: "DeviceSystem", G, stream=None):
     """Descriptors into G without any device allocation (static scratch; see the header)."""
     h = _DescHolder(desc)
     _check(load().panna_descriptors_static(C.byref(h.s), C.byref(sysd.s), _ptr(G), _stream(stream)))
+
+
+def panna_capture(ctx: int, sysd: "DeviceSystem", theta, prec: int, E_cfg, E_atom, F, virial, stream=None):
+    _check(load().panna_capture(ctx, C.byref(sysd.s), _ptr(theta), int(prec), _ptr(E_cfg), _ptr(E_atom), _ptr(F),
+                                _ptr(virial), _stream(stream)))
+
+
+def panna_replay(ctx: int, stream=None):
+    _check(load().panna_replay(ctx, _stream(stream)))
 
 
 def panna_version() -> str:

@@ -450,6 +450,7 @@ def make(name: str, seed: int = 0) -> Workload:
         "fcc1m": lambda: fcc(seed, 64),
         "fcc256": lambda: fcc(seed, 4),
         "fcc4000": lambda: fcc(seed, 10),
+        "fcc32k": lambda: fcc(seed, 20),
         "ragged4096": lambda: ragged(seed, 4096),
         "ragged8": lambda: ragged(seed, 8, 32, 160),
     }

@@ -49,8 +49,10 @@ def descriptor_error(G, Go, desc=None, where=False):
 
 
 def force_error(F, Fo):
+    """max |F - Fo| / RMS(Fo); absolute max when every reference force vanishes."""
     rms = math.sqrt((Fo ** 2).mean())
-    return float(np.abs(F - Fo).max() / rms), rms
+    d = float(np.abs(F - Fo).max()) if F.size else 0.0
+    return (d / rms if rms > 0 else d), rms
 
 
 def layer_errors(archs, g, go):

@@ -179,3 +179,24 @@ def test_results_are_deterministic(torch_cuda):
     E1 = pot.energy_forces(sysd, theta)[0]
     E2 = pot.energy_forces(sysd, theta)[0]
     assert torch.equal(E1, E2)
+
+
+@pytest.mark.parametrize("name", ["molecules16", "fcc256", "ragged8", "tiny_cell"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_adjoint_variants(torch_cuda, name, variant):
+    torch = torch_cuda
+    wl = _special(name)
+    pot = P.Potential(wl.desc, wl.archs)
+    P.panna_set_tuning(pot.ctx, "adjoint", variant)
+    sysd = P.DeviceSystem(wl.system)
+    theta = torch.as_tensor(wl.theta, dtype=torch.float32, device="cuda")
+    E, Ea, F, V = pot.energy_forces(sysd, theta, P.PANNA_MLP_FP32)
+    ref = O.batch(wl.system, wl.desc, wl.archs, wl.theta.astype(np.float32).astype(np.float64))
+    Fn = F.cpu().numpy().astype(np.float64)
+    rms = float(np.sqrt((ref["F"] ** 2).mean()))
+    if rms > 0:
+        assert H.force_error(Fn, ref["F"])[0] <= H.TOL_F_FP32
+    else:
+        assert np.abs(Fn).max() <= 1e-5
+    verr = float(np.abs(V.cpu().numpy() - ref["virial"]).max() / (np.abs(ref["virial"]).max() + 1e-30))
+    assert verr <= 10 * H.TOL_F_FP32
