@@ -11,8 +11,9 @@ library, FP32 kernels and FP64 reductions.  Metric: atoms per second.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (single thread) on a bounded sample of the
-same workload.  Under torchrun each rank runs its own batch (weak scaling); the gradients
-are summed over ranks with one all-reduce per step (data parallel training).
+same workload.  Under torchrun each rank runs its own batch of 1024 molecules (weak
+scaling), normalises its loss by the global counts, and the gradients are summed over
+ranks with one all-reduce per step: the gradient of the global batch (data parallel).
 """
 from __future__ import annotations
 
@@ -188,6 +189,12 @@ def run_ours(args):
     N, C = wl.system.n_atoms, wl.system.n_cfg
     dev = torch.device("cuda", local)
     pot = P.Potential(wl.desc, wl.archs)
+    if world > 1:
+        # every rank normalises its loss by the global counts: the summed gradients are
+        # then exactly those of the global batch (world x 1024 molecules)
+        from paper_2305_11805_gb300 import domain as Dm
+        C_tot, N_tot = Dm.global_counts(C, N)
+        P.panna_set_loss_normalization(pot.ctx, C_tot, N_tot)
     sysd = P.DeviceSystem(wl.system)
     theta = torch.as_tensor(wl.theta.astype(np.float32), device=dev)
     E_ref = torch.as_tensor(wl.e_ref, dtype=torch.float64, device=dev)
@@ -259,6 +266,7 @@ def run_ours(args):
         P.panna_loss_grad(pot.ctx, sys_e2e, theta, d_in[5], d_in[6], wl.w_force, loss, grad)
         if world > 1:
             torch.distributed.all_reduce(grad)
+            torch.distributed.all_reduce(loss)
         h_loss.copy_(loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
 

@@ -118,7 +118,14 @@ typedef struct {
  *   pos      [n_atoms*3] FP64 Cartesian positions (need not be folded into the cell);
  *   species  [n_atoms] int32 in 0..S-1;
  *   cell     [n_cfg*9] FP64, rows are the lattice vectors a, b, c;
- *   pbc      [n_cfg*3] uint8 periodic flags per lattice direction.
+ *   pbc      [n_cfg*3] uint8 periodic flags per lattice direction;
+ *   ghost    [n_atoms] uint8 or NULL.  A ghost atom (ghost[i] != 0) is a neighbour only:
+ *            it is not a centre, so its atomic energy is not part of the sum of Sec. II
+ *            (E_atom[i] = 0), it has an empty neighbour list and a zero descriptor row,
+ *            and the force written for it is only the part -dE/dx_i that the centres of
+ *            this batch exert on it.  Ghosts carry the halo of a spatial decomposition:
+ *            a rank holds its own atoms plus every atom within rc of them as ghosts, and
+ *            the ghost forces are summed into their owners afterwards.  NULL = no ghosts.
  * A configuration with no periodic direction ignores its cell.  Otherwise the cell must
  * be non-singular.  n_cfg and n_atoms are host values.
  */
@@ -130,6 +137,7 @@ typedef struct {
     const int32_t* species;
     const double* cell;
     const uint8_t* pbc;
+    const uint8_t* ghost;
 } panna_system;
 
 typedef struct panna_ctx panna_ctx;
@@ -192,6 +200,16 @@ panna_status panna_set_angular_precision(panna_ctx* ctx, int32_t mode);
  */
 panna_status panna_set_tuning(panna_ctx* ctx, const char* knob, int32_t value);
 
+/*
+ * Normalisers of the training loss (Sec. II.A): with n_cfg_total > 0 and n_atoms_total > 0,
+ * panna_loss_grad divides the energy term by n_cfg_total and the force term by
+ * 3 * n_atoms_total instead of the batch's own counts.  In data-parallel training each
+ * rank passes the global counts, so that the ranks' losses and gradients add up (one
+ * all-reduce) to those of the whole global batch.  (0, 0) restores the default; any other
+ * non-positive value is PANNA_ERR_INVALID_ARG.
+ */
+panna_status panna_set_loss_normalization(panna_ctx* ctx, int64_t n_cfg_total, int64_t n_atoms_total);
+
 /* Synchronise `stream` and return (and clear) the device status word. */
 panna_status panna_check(panna_ctx* ctx, panna_stream_t stream);
 
@@ -235,7 +253,9 @@ panna_status panna_energy_forces(panna_ctx* ctx, const panna_system* sys, const 
  * The force part is the double backward through the networks: with u = dF,
  * w_i = sum_e dG_i/dr_e (u_j(e) - u_i) (descriptor JVP) and g_i = dE_i/dG_i,
  * dtheta += -d/dtheta sum_i g_i . w_i.  Descriptors are recomputed, never stored with
- * their Jacobians (Sec. II.A, on-the-fly descriptors).  FP32 networks only.
+ * their Jacobians (Sec. II.A, on-the-fly descriptors).  FP32 networks only.  With ghost
+ * atoms the sums run over the non-ghost centres, and dF must hold, on each ghost, the
+ * upstream gradient of the atom it stands for (the products then add up over ranks).
  */
 panna_status panna_param_vjp(panna_ctx* ctx, const panna_system* sys, const float* theta,
                              const double* dE, const float* dF, float* dtheta,
@@ -247,7 +267,9 @@ panna_status panna_param_vjp(panna_ctx* ctx, const panna_system* sys, const floa
  *   L = (1/C) sum_c (E_c - E_ref_c)^2 + w_force/(3N) sum_{m,a} (F_ma - F_ref_ma)^2
  * E_ref [n_cfg] FP64 and F_ref [n_atoms*3] FP32 device inputs; outputs (device):
  *   loss [1] FP64, dtheta [P] FP32 = dL/dtheta, and optionally E_cfg [n_cfg] FP64 and
- *   F [n_atoms*3] FP32 (may be NULL).  FP32 networks only.
+ *   F [n_atoms*3] FP32 (may be NULL).  FP32 networks only.  C and N are the batch's own
+ * counts unless panna_set_loss_normalization gave others.  A batch with ghost atoms is
+ * rejected (PANNA_ERR_UNSUPPORTED): its ghost forces are partial sums.
  */
 panna_status panna_loss_grad(panna_ctx* ctx, const panna_system* sys, const float* theta,
                              const double* E_ref, const float* F_ref, double w_force,

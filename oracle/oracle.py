@@ -68,7 +68,7 @@ def lib():
         L.orc_batch.restype = C.c_int
         L.orc_batch.argtypes = [C.c_int64, _i64p, _dp, _i32p, _dp, _u8p, C.POINTER(OrcDesc),
                                 C.POINTER(OrcArch), _dp, _i64p, _dp, _dp, _dp, _dp, _dp,
-                                _dp, _dp, C.c_double, _dp, _dp]
+                                _dp, _dp, C.c_double, _dp, _dp, _u8p, C.c_double, C.c_double]
         L.orc_sampled.restype = C.c_int
         L.orc_sampled.argtypes = [C.c_int64, _dp, _i32p, _dp, _u8p, C.POINTER(OrcDesc),
                                   C.POINTER(OrcArch), _dp, _i64p, C.c_int64, _i64p, C.c_int64,
@@ -177,8 +177,11 @@ def neighbor_list(system, rc: float):
 
 
 def batch(system, desc, archs, theta, want_G: bool = False, e_ref=None, f_ref=None,
-          w_force: float = 0.1, param_grad: bool = False):
-    """Whole-batch FP64 evaluation; returns a dict of numpy arrays (see orc_batch)."""
+          w_force: float = 0.1, param_grad: bool = False, ghost=None, norm=None):
+    """Whole-batch FP64 evaluation; returns a dict of numpy arrays (see orc_batch).
+
+    ghost: optional [n_atoms] flags of atoms that are neighbours only (not centres).
+    norm: optional (C, N) loss normalisers replacing the batch's own counts."""
     s = system
     h = _DescHolder(desc)
     D = lib().orc_descriptor_size(C.byref(h.s))
@@ -197,11 +200,13 @@ def batch(system, desc, archs, theta, want_G: bool = False, e_ref=None, f_ref=No
     fr = None if f_ref is None else np.ascontiguousarray(f_ref, np.float64)
     loss = np.zeros(1)
     dth = np.zeros(len(th)) if (param_grad and er is not None) else None
+    gh = None if ghost is None else np.ascontiguousarray(ghost, np.uint8)
     lib().orc_batch(Cn, _ptr(off, _i64p), _ptr(pos, _dp), _ptr(spec, _i32p), _ptr(cell, _dp),
                     _ptr(pbc, _u8p), C.byref(h.s), arr, _ptr(th, _dp), _ptr(toff, _i64p),
                     _ptr(G, _dp), _ptr(out["E_atom"], _dp), _ptr(out["E_cfg"], _dp),
                     _ptr(out["F"], _dp), _ptr(out["virial"], _dp), _ptr(er, _dp), _ptr(fr, _dp),
-                    float(w_force), _ptr(loss, _dp), _ptr(dth, _dp))
+                    float(w_force), _ptr(loss, _dp), _ptr(dth, _dp), _ptr(gh, _u8p),
+                    float(norm[0]) if norm else 0.0, float(norm[1]) if norm else 0.0)
     if want_G:
         out["G"] = G
     if er is not None:

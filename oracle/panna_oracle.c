@@ -514,10 +514,14 @@ int orc_batch(int64_t n_cfg, const int64_t* atom_off, const double* pos, const i
               const double* cell, const uint8_t* pbc, const orc_desc* p, const orc_arch* archs,
               const double* theta, const int64_t* theta_off,
               double* G_out, double* E_atom, double* E_cfg, double* F, double* virial,
-              const double* E_ref, const double* F_ref, double w_force, double* loss, double* dtheta)
+              const double* E_ref, const double* F_ref, double w_force, double* loss, double* dtheta,
+              const uint8_t* ghost, double c_norm, double n_norm)
 {
     const int D = orc_descriptor_size(p);
     const int64_t N = atom_off[n_cfg];
+    /* Loss normalisers: the batch's own counts unless given (a shard of a larger batch). */
+    const double CN = c_norm > 0.0 ? c_norm : (double)n_cfg;
+    const double NN = n_norm > 0.0 ? n_norm : (double)N;
     orc_work wk;
     memset(&wk, 0, sizeof wk);
     work_fit(&wk, 16, D);
@@ -529,6 +533,13 @@ int orc_batch(int64_t n_cfg, const int64_t* atom_off, const double* pos, const i
         const double* cp = cell + 9 * c; const uint8_t* pp = pbc + 3 * c;
         double ec = 0.0;
         for (int64_t i = 0; i < n; ++i) {
+            /* The energy is a sum over centres (Sec. II); an atom flagged ghost is only a
+             * neighbour, so the sum and its derivatives leave out its own term. */
+            if (ghost && ghost[a0 + i]) {
+                E_atom[a0 + i] = 0.0;
+                if (G_out) memset(G_out + (size_t)(a0 + i) * D, 0, sizeof(double) * D);
+                continue;
+            }
             int64_t k = env(i, n, pos + 3 * a0, species + a0, cp, pp, p->rc, NULL, 0, &wk.nb, &wk.cap);
             work_fit(&wk, k, D);
             for (int64_t e = 0; e < k; ++e) {
@@ -564,17 +575,18 @@ int orc_batch(int64_t n_cfg, const int64_t* atom_off, const double* pos, const i
         double le = 0.0, lf = 0.0;
         for (int64_t c = 0; c < n_cfg; ++c) le += (E_cfg[c] - E_ref[c]) * (E_cfg[c] - E_ref[c]);
         for (int64_t t = 0; t < 3 * N; ++t) lf += (F[t] - F_ref[t]) * (F[t] - F_ref[t]);
-        *loss = le / (double)n_cfg + w_force * lf / (3.0 * (double)N);
+        *loss = le / CN + w_force * lf / (3.0 * NN);
         if (dtheta) {
             int S = p->n_species;
             memset(dtheta, 0, sizeof(double) * theta_off[S]);
             double* u = (double*)malloc(sizeof(double) * 3 * N);
-            for (int64_t t = 0; t < 3 * N; ++t) u[t] = 2.0 * w_force / (3.0 * (double)N) * (F[t] - F_ref[t]);
+            for (int64_t t = 0; t < 3 * N; ++t) u[t] = 2.0 * w_force / (3.0 * NN) * (F[t] - F_ref[t]);
             for (int64_t c = 0; c < n_cfg; ++c) {
                 int64_t a0 = atom_off[c], n = atom_off[c + 1] - a0;
                 const double* cp = cell + 9 * c; const uint8_t* pp = pbc + 3 * c;
-                double alpha = 2.0 / (double)n_cfg * (E_cfg[c] - E_ref[c]);
+                double alpha = 2.0 / CN * (E_cfg[c] - E_ref[c]);
                 for (int64_t i = 0; i < n; ++i) {
+                    if (ghost && ghost[a0 + i]) continue;
                     int64_t k = env(i, n, pos + 3 * a0, species + a0, cp, pp, p->rc, NULL, 0, &wk.nb, &wk.cap);
                     work_fit(&wk, k, D);
                     for (int64_t e = 0; e < k; ++e) {

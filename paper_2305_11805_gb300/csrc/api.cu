@@ -77,6 +77,7 @@ struct panna_ctx {
     int ang_mode = 0;
     int autotune = 1;
     int force_adjoint = -1;
+    int64_t norm_C = 0, norm_N = 0;   // loss normalisers (0 = the batch's own counts)
     int last_launches = 0;
     // autotuner: kernel variant per problem signature, measured on the first call
     struct Tuned { int64_t N, C; int cap, prec, adjoint; };
@@ -364,7 +365,8 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         const double* alpha = nullptr;
         if (rq.train) {
             stage_mark(c, 7, s);
-            CU(launch_loss(L.w, E_cfg, rq.E_ref, F, rq.F_ref, rq.w_force, rq.loss, L.alpha_cfg, L.u, L.loss_part, s, &nl));
+            CU(launch_loss(L.w, c->norm_C, c->norm_N, E_cfg, rq.E_ref, F, rq.F_ref, rq.w_force, rq.loss,
+                           L.alpha_cfg, L.u, L.loss_part, s, &nl));
             u = L.u;
             alpha = L.alpha_cfg;
         } else {
@@ -564,6 +566,17 @@ panna_status panna_set_tuning(panna_ctx* c, const char* knob, int32_t value)
     return fail(PANNA_ERR_INVALID_ARG, "unknown tuning knob or value: %s=%d", knob, value);
 }
 
+panna_status panna_set_loss_normalization(panna_ctx* c, int64_t n_cfg_total, int64_t n_atoms_total)
+{
+    if (!c) return fail(PANNA_ERR_INVALID_ARG, "null context");
+    const bool reset = n_cfg_total == 0 && n_atoms_total == 0;
+    if (!reset && (n_cfg_total <= 0 || n_atoms_total <= 0))
+        return fail(PANNA_ERR_INVALID_ARG, "loss normalisers must both be positive, or both 0");
+    c->norm_C = n_cfg_total;
+    c->norm_N = n_atoms_total;
+    return PANNA_OK;
+}
+
 panna_status panna_check(panna_ctx* c, panna_stream_t stream)
 {
     if (!c) return fail(PANNA_ERR_INVALID_ARG, "null context");
@@ -652,6 +665,8 @@ panna_status panna_loss_grad(panna_ctx* c, const panna_system* sys, const float*
 {
     if (!theta || !E_ref || !F_ref || !loss || !dtheta)
         return fail(PANNA_ERR_INVALID_ARG, "theta, E_ref, F_ref, loss and dtheta are required");
+    if (sys && sys->ghost)
+        return fail(PANNA_ERR_UNSUPPORTED, "the training loss needs complete forces: no ghost atoms");
     Request rq;
     rq.theta = theta; rq.train = true; rq.E_ref = E_ref; rq.F_ref = F_ref; rq.w_force = w_force; rq.loss = loss;
     rq.dtheta = dtheta; rq.E_cfg = E_cfg; rq.F = F; rq.forces = true; rq.energy = true;

@@ -120,9 +120,10 @@ int cfg_chunks(int64_t N, int64_t C);
 cudaError_t launch_cfg_reduce(const Work& w, const float* E_rows, const float* vir_atom, double* E_cfg, double* virial,
                               float* E_atom, double* part, cudaStream_t s, int* launches);
 constexpr int kLossParts = 2 * 120;
-cudaError_t launch_loss(const Work& w, const double* E_cfg, const double* E_ref, const float* F, const float* F_ref,
-                        double w_force, double* loss, double* alpha_cfg, float* u, double* part, cudaStream_t s,
-                        int* launches);
+// C_norm, N_norm <= 0: normalise by the batch's own counts w.C, w.N
+cudaError_t launch_loss(const Work& w, int64_t C_norm, int64_t N_norm, const double* E_cfg, const double* E_ref,
+                        const float* F, const float* F_ref, double w_force, double* loss, double* alpha_cfg, float* u,
+                        double* part, cudaStream_t s, int* launches);
 cudaError_t launch_row_scale(const Work& w, const double* alpha_cfg, float* alpha_rows, cudaStream_t s, int* launches);
 
 // message returned by panna_last_error() on this thread (api.cu)

@@ -248,6 +248,7 @@ __global__ void k_layer_adjoint(LayerArgs la, const int32_t* __restrict__ seg_of
     if (idx >= N * ld) return;
     const int64_t r = idx / ld;
     const int c = (int)(idx % ld);
+    if (r >= seg_off[la.S]) return;     // rows past the last species (ghost atoms have none)
     int s = 0;
     while (s < la.S - 1 && r >= seg_off[s + 1]) ++s;
     if (c >= la.N[s]) return;

@@ -375,7 +375,7 @@ __global__ void k_out_layer(int S, const int32_t* __restrict__ seg_off, int64_t 
 {
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (r >= N) return;
+    if (r >= N || r >= seg_off[S]) return;     // rows past the last species (ghost atoms have none)
     int s = 0;
     while (s < S - 1 && r >= seg_off[s + 1]) ++s;
     const int H = lo.K[s];

@@ -378,8 +378,8 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
             const int32_t* __restrict__ atom_cfg, const int32_t* __restrict__ atom_cell,
             const int64_t* __restrict__ cell_start, const int32_t* __restrict__ cell_atoms,
             const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo, int cap,
-            int32_t* __restrict__ nb_count, float4* __restrict__ nb_vec, int2* __restrict__ nb_idx,
-            DevStatus* st)
+            const uint8_t* __restrict__ ghost, int32_t* __restrict__ nb_count, float4* __restrict__ nb_vec,
+            int2* __restrict__ nb_idx, DevStatus* st)
 {
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -387,6 +387,10 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
     int2* sidx = reinterpret_cast<int2*>(reinterpret_cast<float4*>(smem_raw) + (size_t)kNbWarps * cap) + (size_t)warp * cap;
     const int64_t i = (int64_t)blockIdx.x * kNbWarps + warp;
     if (i >= N) return;
+    if (ghost && ghost[i]) {          // a ghost is a neighbour only, never a centre
+        if (lane == 0) nb_count[i] = 0;
+        return;
+    }
     const int c = atom_cfg[i];
     const CfgGeom& g = geom[c];
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
@@ -567,7 +571,7 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
     if (nbW == 0) nbW = 1;
     k_neighbors<<<nbW, kNbWarps * 32, smem, s>>>(N, d.S, d.rc_d, d.rc, w.geom, w.atom_cfg, w.atom_cell,
                                                  w.cell_start, w.cell_atoms, w.pos_hi, w.pos_lo, w.cap,
-                                                 w.nb_count, w.nb_vec, w.nb_idx, w.status);
+                                                 w.sys->ghost, w.nb_count, w.nb_vec, w.nb_idx, w.status);
     ++*launches;
     return cudaGetLastError();
 }
@@ -576,13 +580,15 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
 
 constexpr int kSpBlock = 1024;
 
-__global__ void k_species_count(int64_t N, int S, const float4* __restrict__ pos_hi, int32_t* __restrict__ blk_counts)
+// Rows of the networks: the non-ghost atoms grouped by species (ghosts get row -1).
+__global__ void k_species_count(int64_t N, int S, const float4* __restrict__ pos_hi, const uint8_t* __restrict__ ghost,
+                                int32_t* __restrict__ blk_counts)
 {
     __shared__ int cnt[kMaxSpecies];
     if (threadIdx.x < kMaxSpecies) cnt[threadIdx.x] = 0;
     __syncthreads();
     int64_t i = (int64_t)blockIdx.x * kSpBlock + threadIdx.x;
-    if (i < N) atomicAdd(&cnt[__float_as_int(pos_hi[i].w)], 1);
+    if (i < N && !(ghost && ghost[i])) atomicAdd(&cnt[__float_as_int(pos_hi[i].w)], 1);
     __syncthreads();
     if (threadIdx.x < S) blk_counts[(size_t)blockIdx.x * S + threadIdx.x] = cnt[threadIdx.x];
 }
@@ -610,14 +616,14 @@ __global__ void k_species_offsets(int64_t nblk, int S, int32_t* __restrict__ blk
     }
 }
 
-__global__ void k_species_rank(int64_t N, int S, const float4* __restrict__ pos_hi,
+__global__ void k_species_rank(int64_t N, int S, const float4* __restrict__ pos_hi, const uint8_t* __restrict__ ghost,
                                const int32_t* __restrict__ blk_off, int32_t* __restrict__ row_of_atom,
                                int32_t* __restrict__ atom_of_row)
 {
     __shared__ int wcnt[kSpBlock / 32][kMaxSpecies];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t i = (int64_t)blockIdx.x * kSpBlock + threadIdx.x;
-    int sp = i < N ? __float_as_int(pos_hi[i].w) : -1;
+    int sp = (i < N && !(ghost && ghost[i])) ? __float_as_int(pos_hi[i].w) : -1;
     int my_rank = 0;
     for (int s = 0; s < S; ++s) {
         unsigned m = __ballot_sync(0xffffffffu, sp == s);
@@ -625,7 +631,8 @@ __global__ void k_species_rank(int64_t N, int S, const float4* __restrict__ pos_
         if (lane == 0) wcnt[wid][s] = __popc(m);
     }
     __syncthreads();
-    if (i < N) {
+    if (i < N && sp < 0) row_of_atom[i] = -1;
+    if (i < N && sp >= 0) {
         int before = 0;
         for (int w2 = 0; w2 < wid; ++w2) before += wcnt[w2][sp];
         int row = blk_off[(size_t)blockIdx.x * S + sp] + before + my_rank;
@@ -638,9 +645,11 @@ cudaError_t species_order(Work& w, int S, cudaStream_t s, int* launches)
 {
     int64_t nblk = (w.N + kSpBlock - 1) / kSpBlock;
     if (nblk == 0) nblk = 1;
-    k_species_count<<<(unsigned)nblk, kSpBlock, 0, s>>>(w.N, S, w.pos_hi, w.blk_counts);
+    const uint8_t* ghost = w.sys->ghost;
+    k_species_count<<<(unsigned)nblk, kSpBlock, 0, s>>>(w.N, S, w.pos_hi, ghost, w.blk_counts);
     k_species_offsets<<<1, 32, 0, s>>>(nblk, S, w.blk_counts, w.seg_off);
-    k_species_rank<<<(unsigned)nblk, kSpBlock, 0, s>>>(w.N, S, w.pos_hi, w.blk_counts, w.row_of_atom, w.atom_of_row);
+    k_species_rank<<<(unsigned)nblk, kSpBlock, 0, s>>>(w.N, S, w.pos_hi, ghost, w.blk_counts, w.row_of_atom,
+                                                      w.atom_of_row);
     *launches += 3;
     return cudaGetLastError();
 }

@@ -43,8 +43,10 @@ k_cfg_partial(int64_t C, const int64_t* __restrict__ atom_off, int B, const int3
 #pragma unroll
     for (int k = 0; k < kCfgVals; ++k) v[k] = 0.0;
     for (int64_t i = s0 + lane; i < s1; i += 32) {
-        const float e = E_rows[row_of_atom[i]];
+        const int row = row_of_atom[i];
+        const float e = row >= 0 ? E_rows[row] : 0.f;     // a ghost (row -1) adds nothing
         if (E_atom) E_atom[i] = e;
+        if (row < 0) continue;
         v[0] += e;
         if (vir_atom)
 #pragma unroll
@@ -96,18 +98,21 @@ cudaError_t launch_cfg_reduce(const Work& w, const float* E_rows, const float* v
 
 constexpr int kLossBlocks = 120;
 
-__global__ void k_loss_partial(int64_t C, int64_t N, const double* __restrict__ E_cfg, const double* __restrict__ E_ref,
-                               const float* __restrict__ F, const float* __restrict__ F_ref, double w_force,
-                               double* __restrict__ part, double* __restrict__ alpha_cfg, float* __restrict__ u)
+// C_norm and N_norm are the loss normalisers: the batch's own counts, or the global counts
+// of a data-parallel batch split over ranks
+__global__ void k_loss_partial(int64_t C, int64_t N, double C_norm, double N_norm, const double* __restrict__ E_cfg,
+                               const double* __restrict__ E_ref, const float* __restrict__ F,
+                               const float* __restrict__ F_ref, double w_force, double* __restrict__ part,
+                               double* __restrict__ alpha_cfg, float* __restrict__ u)
 {
     double le = 0.0, lf = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double cu = 2.0 * w_force / (3.0 * (double)N);
+    const double cu = 2.0 * w_force / (3.0 * N_norm);
     for (int64_t c = t0; c < C; c += stride) {
         double r = E_cfg[c] - E_ref[c];
         le += r * r;
-        alpha_cfg[c] = 2.0 * r / (double)C;
+        alpha_cfg[c] = 2.0 * r / C_norm;
     }
     for (int64_t k = t0; k < 3 * N; k += stride) {
         double r = (double)F[k] - (double)F_ref[k];
@@ -119,7 +124,8 @@ __global__ void k_loss_partial(int64_t C, int64_t N, const double* __restrict__ 
     if (threadIdx.x == 0) { part[2 * blockIdx.x] = a; part[2 * blockIdx.x + 1] = b; }
 }
 
-__global__ void k_loss_final(int64_t C, int64_t N, double w_force, const double* __restrict__ part, double* __restrict__ loss)
+__global__ void k_loss_final(double C_norm, double N_norm, double w_force, const double* __restrict__ part,
+                             double* __restrict__ loss)
 {
     const int lane = threadIdx.x & 31;
     double le = 0.0, lf = 0.0;
@@ -129,15 +135,17 @@ __global__ void k_loss_final(int64_t C, int64_t N, double w_force, const double*
         le += __shfl_xor_sync(0xffffffffu, le, o);
         lf += __shfl_xor_sync(0xffffffffu, lf, o);
     }
-    if (lane == 0 && blockIdx.x == 0) *loss = le / (double)C + w_force * lf / (3.0 * (double)N);
+    if (lane == 0 && blockIdx.x == 0) *loss = le / C_norm + w_force * lf / (3.0 * N_norm);
 }
 
-cudaError_t launch_loss(const Work& w, const double* E_cfg, const double* E_ref, const float* F, const float* F_ref,
-                        double w_force, double* loss, double* alpha_cfg, float* u, double* part, cudaStream_t s,
-                        int* launches)
+cudaError_t launch_loss(const Work& w, int64_t C_norm, int64_t N_norm, const double* E_cfg, const double* E_ref,
+                        const float* F, const float* F_ref, double w_force, double* loss, double* alpha_cfg, float* u,
+                        double* part, cudaStream_t s, int* launches)
 {
-    k_loss_partial<<<kLossBlocks, kRedThreads, 0, s>>>(w.C, w.N, E_cfg, E_ref, F, F_ref, w_force, part, alpha_cfg, u);
-    k_loss_final<<<1, 32, 0, s>>>(w.C, w.N, w_force, part, loss);
+    const double cn = (double)(C_norm > 0 ? C_norm : w.C), nn = (double)(N_norm > 0 ? N_norm : w.N);
+    k_loss_partial<<<kLossBlocks, kRedThreads, 0, s>>>(w.C, w.N, cn, nn, E_cfg, E_ref, F, F_ref, w_force, part,
+                                                       alpha_cfg, u);
+    k_loss_final<<<1, 32, 0, s>>>(cn, nn, w_force, part, loss);
     *launches += 2;
     return cudaGetLastError();
 }
@@ -147,7 +155,7 @@ __global__ void k_alpha_rows(int64_t N, const int32_t* __restrict__ atom_cfg, co
                              const double* __restrict__ alpha_cfg, float* __restrict__ alpha_rows)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (i >= N || row_of_atom[i] < 0) return;
     alpha_rows[row_of_atom[i]] = alpha_cfg ? (float)alpha_cfg[atom_cfg[i]] : 0.f;
 }
 

@@ -43,7 +43,7 @@ class panna_mlp_arch(C.Structure):
 
 class panna_system(C.Structure):
     _fields_ = [("n_cfg", C.c_int64), ("n_atoms", C.c_int64), ("atom_off", _vp), ("pos", _vp),
-                ("species", _vp), ("cell", _vp), ("pbc", _vp)]
+                ("species", _vp), ("cell", _vp), ("pbc", _vp), ("ghost", _vp)]
 
 
 class PannaError(RuntimeError):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
         "panna_check": (i32, [_vp, _vp]),
         "panna_set_angular_precision": (i32, [_vp, i32]),
         "panna_set_tuning": (i32, [_vp, C.c_char_p, i32]),
+        "panna_set_loss_normalization": (i32, [_vp, i64, i64]),
         "panna_neighbors": (i32, [_vp, C.POINTER(panna_system), i64, _vp, _vp, _vp, C.POINTER(i64), _vp]),
         "panna_descriptors": (i32, [_vp, C.POINTER(panna_system), _vp, _vp]),
         "panna_energy_forces": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
@@ -101,7 +102,8 @@ def load(path: str = LIB_PATH):
 def exported_symbols() -> Sequence[str]:
     return ["panna_version", "panna_last_error", "panna_descriptor_size", "panna_create", "panna_destroy",
             "panna_param_count", "panna_set_neighbor_capacity", "panna_neighbor_capacity", "panna_set_async",
-            "panna_check", "panna_set_angular_precision", "panna_set_tuning", "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
+            "panna_check", "panna_set_angular_precision", "panna_set_tuning", "panna_set_loss_normalization",
+            "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
             "panna_descriptors_static", "panna_capture", "panna_replay"]
 
@@ -184,6 +186,10 @@ def panna_set_tuning(ctx: int, knob: str, value: int):
     _check(load().panna_set_tuning(ctx, knob.encode(), int(value)))
 
 
+def panna_set_loss_normalization(ctx: int, n_cfg_total: int, n_atoms_total: int):
+    _check(load().panna_set_loss_normalization(ctx, int(n_cfg_total), int(n_atoms_total)))
+
+
 def panna_check(ctx: int, stream=None):
     _check(load().panna_check(ctx, _stream(stream)))
 
@@ -251,26 +257,28 @@ def panna_version() -> str:
 class DeviceSystem:
     """Device copies (torch CUDA tensors) of a workloads.System plus the C struct."""
 
-    def __init__(self, system, device="cuda"):
+    def __init__(self, system, device="cuda", ghost=None):
         import torch
         self.atom_off = torch.as_tensor(np.ascontiguousarray(system.atom_off, np.int64), device=device)
         self.pos = torch.as_tensor(np.ascontiguousarray(system.pos, np.float64), device=device)
         self.species = torch.as_tensor(np.ascontiguousarray(system.species, np.int32), device=device)
         self.cell = torch.as_tensor(np.ascontiguousarray(system.cell, np.float64), device=device)
         self.pbc = torch.as_tensor(np.ascontiguousarray(system.pbc, np.uint8), device=device)
+        self.ghost = None if ghost is None else torch.as_tensor(np.ascontiguousarray(ghost, np.uint8), device=device)
         self.n_cfg = int(system.n_cfg)
         self.n_atoms = int(system.n_atoms)
         self.s = panna_system(self.n_cfg, self.n_atoms, self.atom_off.data_ptr(), self.pos.data_ptr(),
-                              self.species.data_ptr(), self.cell.data_ptr(), self.pbc.data_ptr())
+                              self.species.data_ptr(), self.cell.data_ptr(), self.pbc.data_ptr(), _ptr(self.ghost))
 
     @classmethod
-    def from_tensors(cls, atom_off, pos, species, cell, pbc):
+    def from_tensors(cls, atom_off, pos, species, cell, pbc, ghost=None):
         obj = cls.__new__(cls)
         obj.atom_off, obj.pos, obj.species, obj.cell, obj.pbc = atom_off, pos, species, cell, pbc
+        obj.ghost = ghost
         obj.n_cfg = int(atom_off.shape[0] - 1)
         obj.n_atoms = int(pos.shape[0])
         obj.s = panna_system(obj.n_cfg, obj.n_atoms, atom_off.data_ptr(), pos.data_ptr(), species.data_ptr(),
-                             cell.data_ptr(), pbc.data_ptr())
+                             cell.data_ptr(), pbc.data_ptr(), _ptr(ghost))
         return obj
 
 

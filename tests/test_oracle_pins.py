@@ -438,6 +438,63 @@ def test_loss_parameter_gradient_fd():
         assert not np.any(g[off[s]:off[s + 1]])
 
 
+def test_ghost_mask_partial_sum_and_forces_fd():
+    # Atoms flagged ghost are neighbours only (the halo of a spatial decomposition): the
+    # energy is the sum of the OTHER atoms' energies of the unmasked evaluation, the forces
+    # are minus its derivative on every atom, ghosts included (central differences), and
+    # they still sum to zero (the partial sum is translation invariant).
+    wl, sysm = _small_periodic(1)
+    full = O.batch(sysm, wl.desc, wl.archs, wl.theta)
+    rng = np.random.default_rng(4)
+    ghost = (rng.random(sysm.n_atoms) < 0.4).astype(np.uint8)
+    assert 0 < ghost.sum() < sysm.n_atoms
+    out = O.batch(sysm, wl.desc, wl.archs, wl.theta, ghost=ghost)
+    assert not np.any(out["E_atom"][ghost == 1])
+    np.testing.assert_allclose(out["E_atom"][ghost == 0], full["E_atom"][ghost == 0], rtol=1e-13)
+    assert abs(out["E_cfg"][0] - full["E_atom"][ghost == 0].sum()) < 1e-10 * np.abs(full["E_atom"]).sum()
+    F = out["F"]
+    np.testing.assert_allclose(F.sum(0), 0.0, atol=1e-10 * np.abs(F).max())
+    h = 1e-5
+    for m in [int(np.nonzero(ghost)[0][0]), int(np.nonzero(ghost == 0)[0][0])]:
+        for c in range(3):
+            vals = []
+            for sgn in (1, -1):
+                p = sysm.pos.copy(); p[m, c] += sgn * h
+                s2 = W.System(sysm.atom_off, p, sysm.species, sysm.cell, sysm.pbc, sysm.n_species)
+                vals.append(O.batch(s2, wl.desc, wl.archs, wl.theta, ghost=ghost)["E_cfg"].sum())
+            assert abs(-(vals[0] - vals[1]) / (2 * h) - F[m, c]) < 1e-6 * np.abs(F).max(), (m, c)
+
+
+def test_loss_normalisers_closed_form_and_fd():
+    # A shard of a larger batch normalises its loss terms by the global counts (C', N'):
+    # L = sum_c (E_c - E_ref)^2 / C' + w sum (F - F_ref)^2 / (3 N'), recomputed here from the
+    # returned energies and forces, and dL/dtheta against central differences of that loss.
+    wl = W.make("molecules16")
+    sysm = wl.system.subset([3, 4])
+    d = W.descriptor_params(4, 5.2, 6, 3, 2)
+    archs = [W._mlp(d.D, (5, 3)) for _ in range(4)]
+    rng = np.random.default_rng(12)
+    theta = W.init_weights(rng, d, archs, 2.0, 2.0)
+    e_ref = rng.normal(size=2)
+    f_ref = rng.normal(size=(sysm.n_atoms, 3))
+    norm = (7, 5 * sysm.n_atoms + 3)
+    out = O.batch(sysm, d, archs, theta, e_ref=e_ref, f_ref=f_ref, w_force=0.3, param_grad=True, norm=norm)
+    want = ((out["E_cfg"] - e_ref) ** 2).sum() / norm[0] + 0.3 * ((out["F"] - f_ref) ** 2).sum() / (3 * norm[1])
+    assert abs(out["loss"] - want) < 1e-12 * want
+    g = out["dtheta"]
+    h = 1e-6
+    off = W.param_offsets(archs)
+    idx = []
+    for s in set(sysm.species.tolist()):
+        idx += list(rng.choice(np.arange(off[s], off[s + 1]), 6, replace=False))
+    for k in idx:
+        tp = theta.copy(); tp[k] += h
+        tm = theta.copy(); tm[k] -= h
+        lp = O.batch(sysm, d, archs, tp, e_ref=e_ref, f_ref=f_ref, w_force=0.3, norm=norm)["loss"]
+        lm = O.batch(sysm, d, archs, tm, e_ref=e_ref, f_ref=f_ref, w_force=0.3, norm=norm)["loss"]
+        assert abs((lp - lm) / (2 * h) - g[k]) < 1e-6 * max(1.0, abs(g[k])) + 1e-7 * np.abs(g).max(), k
+
+
 def test_sampled_matches_batch():
     wl = W.make("fcc256")
     full = O.batch(wl.system, wl.desc, wl.archs, wl.theta, want_G=True)
