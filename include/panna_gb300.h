@@ -181,8 +181,9 @@ panna_status panna_set_async(panna_ctx* ctx, int32_t async);
 
 /*
  * Arithmetic of the angular descriptor terms (descriptor, adjoint, JVP):
- *   0 = automatic (default): extended precision with FP32 networks (force tolerance 1e-5 of
- *       RMS), plain FP32 with the BF16 modes (their tolerance is 1e-2);
+ *   0 = automatic (default): extended precision for the descriptor and the adjoint with FP32
+ *       networks (force tolerance 1e-5 of RMS), plain FP32 with the BF16 modes (their
+ *       tolerance is 1e-2) and for the JVP of the weight gradient (tolerance 1e-4);
  *   1 = extended: unit vectors, cos/sin of the angle and (1 + cos(theta - theta_m))/2
  *       carried as pairs of floats (about 4x smaller error under the zeta-th power,
  *       about twice the arithmetic);
@@ -194,9 +195,20 @@ panna_status panna_set_angular_precision(panna_ctx* ctx, int32_t mode);
  * Kernel variants and the autotuner.  knob "autotune": 1 (default) = on the first
  * synchronous call for a given problem signature (atoms, configurations, neighbour
  * capacity, precision) time the candidate variants on the caller's stream and keep the
- * fastest; 0 = use a fixed rule.  knob "adjoint": -1 (default) = tuned, 0 = pairs by
- * species block (8 warps per CTA), 1 = all pairs of an atom in one flattened range (4 warps
- * per CTA).  Returns PANNA_ERR_INVALID_ARG for an unknown knob or value.
+ * fastest; 0 = use a fixed rule (flattened with several species, blocked with one).
+ * knobs "descriptor", "adjoint", "jvp" (the three kernels over angular pairs): -1 (default)
+ * = tuned, 0 = pairs by species block (8 warps per CTA), 1 = all pairs of an atom in one
+ * flattened range (4 warps per CTA; shared-memory atomics make the sums reproducible to
+ * rounding rather than bit for bit).  knob "mlp_fp32" (PANNA_MLP_FP32 networks): a bit mask of the first layer's
+ * products (descriptor width to first hidden width, almost all of the networks'
+ * arithmetic) that run on the tensor cores with operands split into TF32 parts, the rest
+ * staying on the CUDA cores in plain FP32: 1 = forward (three parts), 2 = input gradient
+ * dE/dG (three parts), 4 = tangent of the weight-gradient pass (two parts), 8 = weight
+ * gradient (two parts).  Default 4 | 8 = 12: the training-only products, so that energies
+ * and forces are those of the plain FP32 path; the tensor cores' accumulation makes the
+ * forward product about 6x less accurate than an FP32 dot product rounded to nearest.
+ * 0 = everything on the CUDA cores.  Returns PANNA_ERR_INVALID_ARG for an unknown knob or
+ * value.
  */
 panna_status panna_set_tuning(panna_ctx* ctx, const char* knob, int32_t value);
 

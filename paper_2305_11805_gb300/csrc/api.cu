@@ -76,11 +76,12 @@ struct panna_ctx {
     int profiling = 0;
     int ang_mode = 0;
     int autotune = 1;
-    int force_adjoint = -1;
+    int force_variant[3] = {-1, -1, -1};   // descriptor, adjoint, jvp: -1 = tuned
+    int fp32_tc = TF32_TAN | TF32_WGRAD;   // FP32 networks: first-layer products on the tensor cores
     int64_t norm_C = 0, norm_N = 0;   // loss normalisers (0 = the batch's own counts)
     int last_launches = 0;
     // autotuner: kernel variant per problem signature, measured on the first call
-    struct Tuned { int64_t N, C; int cap, prec, adjoint; };
+    struct Tuned { int64_t N, C; int cap, prec; int variant[3]; };   // -1 = not measured yet
     Tuned tuned[16];
     int n_tuned = 0;
     cudaEvent_t tev[3] = {};
@@ -119,9 +120,17 @@ struct Layout {
     float* wdot = nullptr;
     double* loss_part = nullptr;
     void* tc_ws = nullptr;   // BF16 tensor-core network buffers
+    void* tf_ws = nullptr;   // FP32 networks: TF32 first-layer buffers
 };
 
 constexpr int kSplits = 16;
+
+// TF32_* products of the first layer that run on the tensor cores in this evaluation
+int tf32_mask(const panna_ctx* c, bool bf16, bool train)
+{
+    if (bf16 || !tf32_first_layer_ok(c->plan)) return 0;
+    return c->fp32_tc & (train ? (TF32_FWD | TF32_INGRAD | TF32_TAN | TF32_WGRAD) : (TF32_FWD | TF32_INGRAD));
+}
 
 void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, Layout& L)
 {
@@ -170,6 +179,7 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, 
     b.tile_start = a.take<int32_t>(S + 1);
     b.splits = kSplits;
     if (bf16) L.tc_ws = a.take<char>(tc_workspace_bytes(p, N, true));
+    if (const int m = tf32_mask(c, bf16, train)) L.tf_ws = a.take<char>(tf32_workspace_bytes(p, N, m));
     if (train) {
         for (int l = 1; l <= p.L; ++l) {
             b.Zd[l] = a.take<float>((size_t)N * p.ld[l]);
@@ -287,30 +297,39 @@ struct Request {
     float* dtheta = nullptr;
 };
 
-// Adjoint variant for this problem signature: measured once (both variants into scratch
-// forces, CUDA events on the caller's stream), then cached.  Asynchronous calls never
-// measure (they may be under stream capture) and use the cached or default choice.
-int tuned_adjoint(panna_ctx* c, const panna_system* sys, int prec, const Layout& L, bool acc, cudaStream_t s)
+// Kernel variants (0 blocked, 1 flattened) of the descriptor-family kernels for this problem
+// signature: measured once per kernel (each variant launched once to warm up, then timed
+// with CUDA events on the caller's stream), then cached.  Asynchronous calls never measure
+// (they may be under stream capture) and use the cached or default choice.
+enum { KV_DESC = 0, KV_ADJ = 1, KV_JVP = 2 };
+
+template <class Launch>
+int tuned_variant(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch)
 {
-    if (c->force_adjoint >= 0) return c->force_adjoint;
+    if (c->force_variant[kind] >= 0) return c->force_variant[kind];
+    panna_ctx::Tuned* t = nullptr;
     for (int k = 0; k < c->n_tuned; ++k) {
-        const panna_ctx::Tuned& t = c->tuned[k];
-        if (t.N == sys->n_atoms && t.C == sys->n_cfg && t.cap == c->cap && t.prec == prec) return t.adjoint;
+        panna_ctx::Tuned& q = c->tuned[k];
+        if (q.N == sys->n_atoms && q.C == sys->n_cfg && q.cap == c->cap && q.prec == prec) t = &q;
     }
+    if (t && t->variant[kind] >= 0) return t->variant[kind];
     const int fallback = c->d.S > 1 ? 1 : 0;
     if (!c->autotune || c->async || sys->n_atoms == 0) return fallback;
     float ms[2] = {0.f, 0.f};
-    int dummy = 0;
+    for (int v = 0; v < 2; ++v) launch(v);   // first launches load and configure the kernels
     for (int v = 0; v < 2; ++v) {
         cudaEventRecord(c->tev[0], s);
-        launch_adjoint(L.w, c->d, L.g, L.F_tune, nullptr, acc, v, s, &dummy);
+        launch(v);
         cudaEventRecord(c->tev[1], s);
         cudaEventSynchronize(c->tev[1]);
         cudaEventElapsedTime(&ms[v], c->tev[0], c->tev[1]);
     }
     const int best = ms[1] < ms[0] ? 1 : 0;
-    panna_ctx::Tuned t{sys->n_atoms, sys->n_cfg, c->cap, prec, best};
-    c->tuned[c->n_tuned < 16 ? c->n_tuned++ : 15] = t;
+    if (!t) {
+        t = &c->tuned[c->n_tuned < 16 ? c->n_tuned++ : 15];
+        *t = panna_ctx::Tuned{sys->n_atoms, sys->n_cfg, c->cap, prec, {-1, -1, -1}};
+    }
+    t->variant[kind] = best;
     return best;
 }
 
@@ -336,24 +355,47 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     CU(species_order(L.w, c->d.S, s, &nl));
     CU(mlp_tiles(c->plan, L.w.seg_off, L.mb.tile_start, s, &nl));
     stage_mark(c, 1, s);
-    CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl));
+    {
+        int dummy = 0;
+        const int v = tuned_variant(c, sys, rq.prec, KV_DESC, s, [&](int vv) {
+            launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &dummy, vv);
+        });
+        CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl, v));
+    }
     stage_mark(c, 2, s);
     float* F = rq.F ? rq.F : L.F_int;
     double* E_cfg = rq.E_cfg ? rq.E_cfg : L.E_cfg_int;
     const bool need_forces = rq.forces || rq.train;
     const bool tc = rq.prec == PANNA_MLP_BF16 || rq.prec == PANNA_MLP_BF16_FAST;
+    const int tfm = tf32_mask(c, tc, grad);
+    const bool tf = tfm != 0;
     if (tc) {
         // BF16 operands on the tensor cores: energies and dE/dG together
         CU(mlp_bf16_energy_grad(c->plan, L.mb, rq.theta, N, L.tc_ws, rq.prec == PANNA_MLP_BF16, L.E_rows, L.g,
                                 L.w.status, s, &nl));
+    } else if (tf) {
+        // FP32 networks: first-layer products on the tensor cores (TF32 parts), the rest on CUDA cores
+        CU(tf32_prepare(c->plan, L.mb, rq.theta, N, L.tf_ws, tfm, s, &nl));
+        if (tfm & TF32_FWD) CU(tf32_forward1(c->plan, L.mb, N, L.tf_ws, tfm, L.w.status, s, &nl));
+        CU(mlp_forward(c->plan, L.mb, rq.theta, N, s, &nl, (tfm & TF32_FWD) ? 1 : 0));
+        CU(mlp_energy_rows(c->plan, L.mb, N, L.E_rows, s, &nl));
     } else {
         CU(mlp_forward(c->plan, L.mb, rq.theta, N, s, &nl));
         CU(mlp_energy_rows(c->plan, L.mb, N, L.E_rows, s, &nl));
     }
     if (need_forces) {
-        if (!tc) CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl));
+        if (tf && (tfm & TF32_INGRAD)) {
+            float* ab1 = nullptr;
+            CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl, &ab1));
+            CU(tf32_input_grad1(c->plan, L.mb, N, L.tf_ws, tfm, ab1, L.g, L.w.status, s, &nl));
+        } else if (!tc) {
+            CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl));
+        }
         stage_mark(c, 3, s);
-        const int variant = tuned_adjoint(c, sys, rq.prec, L, acc, s);
+        int dummy = 0;
+        const int variant = tuned_variant(c, sys, rq.prec, KV_ADJ, s, [&](int vv) {
+            launch_adjoint(L.w, c->d, L.g, L.F_tune, nullptr, acc, vv, s, &dummy);
+        });
         CU(cudaMemsetAsync(F, 0, sizeof(float) * 3 * N, s));
         CU(launch_adjoint(L.w, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, acc, variant, s, &nl));
     }
@@ -376,12 +418,22 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         CU(launch_row_scale(L.w, alpha, L.alpha_rows, s, &nl));
         stage_mark(c, 5, s);
         if (u) {
-            CU(launch_jvp(L.w, c->d, u, L.wdot, acc, s, &nl));
+            // the tangent enters only the weight gradient (tolerance 1e-4 against 1e-5 for
+            // forces): the plain FP32 angular form unless extended precision is forced
+            const bool acc_jvp = c->ang_mode == 1;
+            int dummy = 0;
+            const int v = tuned_variant(c, sys, rq.prec, KV_JVP, s, [&](int vv) {
+                launch_jvp(L.w, c->d, u, L.wdot, acc_jvp, s, &dummy, vv);
+            });
+            CU(launch_jvp(L.w, c->d, u, L.wdot, acc_jvp, s, &nl, v));
         } else {
             CU(cudaMemsetAsync(L.wdot, 0, sizeof(float) * (size_t)N * c->d.D, s));
         }
         stage_mark(c, 6, s);
-        CU(mlp_param_grad(c->plan, L.mb, rq.theta, N, L.wdot, L.alpha_rows, rq.dtheta, s, &nl));
+        const bool tan_tc = tf && (tfm & TF32_TAN);
+        const WgradTc wtc{(tf && (tfm & TF32_WGRAD)) ? L.tf_ws : nullptr, tfm, L.w.status};
+        if (tan_tc) CU(tf32_tangent1(c->plan, L.mb, N, L.tf_ws, tfm, L.wdot, L.w.status, s, &nl));
+        CU(mlp_param_grad(c->plan, L.mb, rq.theta, N, L.wdot, L.alpha_rows, rq.dtheta, s, &nl, tan_tc, &wtc));
     }
     if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
     return PANNA_OK;
@@ -559,8 +611,14 @@ panna_status panna_set_tuning(panna_ctx* c, const char* knob, int32_t value)
         c->n_tuned = 0;
         return PANNA_OK;
     }
-    if (strcmp(knob, "adjoint") == 0 && value >= -1 && value <= 1) {
-        c->force_adjoint = value;
+    const char* kinds[3] = {"descriptor", "adjoint", "jvp"};
+    for (int k = 0; k < 3; ++k)
+        if (strcmp(knob, kinds[k]) == 0 && value >= -1 && value <= 1) {
+            c->force_variant[k] = value;
+            return PANNA_OK;
+        }
+    if (strcmp(knob, "mlp_fp32") == 0 && value >= 0 && value <= 15) {
+        c->fp32_tc = value;
         return PANNA_OK;
     }
     return fail(PANNA_ERR_INVALID_ARG, "unknown tuning knob or value: %s=%d", knob, value);

@@ -106,14 +106,15 @@ cudaError_t export_neighbors(const Work& w, int64_t* off, int64_t* nbr_j, int32_
 
 // descriptor family (descriptor.cu); row_map == nullptr writes row i for atom i
 // acc selects the extended-precision angular evaluation (see descriptor.cu)
-cudaError_t launch_descriptor(const Work& w, const DescDev& d, float* G_rows, const int32_t* row_map, bool acc,
-                              cudaStream_t s, int* launches);
 // variant 0: pairs by species block, 8 warps per CTA; 1: all pairs of an atom in one
-// flattened range, 4 warps per CTA (full lanes for many small blocks)
+// flattened range, 4 warps per CTA (full lanes for many small blocks); variant 1 falls back
+// to 0 when its shared memory does not fit
+cudaError_t launch_descriptor(const Work& w, const DescDev& d, float* G_rows, const int32_t* row_map, bool acc,
+                              cudaStream_t s, int* launches, int variant = 0);
 cudaError_t launch_adjoint(const Work& w, const DescDev& d, const float* g_rows, float* F, float* vir_atom, bool acc,
                            int variant, cudaStream_t s, int* launches);
 cudaError_t launch_jvp(const Work& w, const DescDev& d, const float* u, float* wdot_rows, bool acc, cudaStream_t s,
-                       int* launches);
+                       int* launches, int variant = 0);
 
 // reductions (reduce.cu)
 int cfg_chunks(int64_t N, int64_t C);

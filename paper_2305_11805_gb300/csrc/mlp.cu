@@ -300,9 +300,9 @@ cudaError_t mlp_tiles(const MlpPlan& p, const int32_t* seg_off, int32_t* tile_st
 }
 
 cudaError_t mlp_forward(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, cudaStream_t s,
-                        int* launches)
+                        int* launches, int l0)
 {
-    for (int l = 0; l < p.L; ++l) {
+    for (int l = l0; l < p.L; ++l) {
         LayerArgs la = layer_args(p, l, false);
         const float* Ain = l == 0 ? b.G : b.A[l];
         const int lda = p.ld[l];
@@ -315,14 +315,15 @@ cudaError_t mlp_forward(const MlpPlan& p, const MlpBuffers& b, const float* thet
 }
 
 cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, float* g,
-                           cudaStream_t s, int* launches)
+                           cudaStream_t s, int* launches, float** ab1)
 {
     // seed dE/da_L = 1, then a_{l-1}bar = (a_l bar * act'(z_l)) W_l
     k_seed<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, p.ld[p.L], nullptr, 0.f, b.Ab, nullptr);
     ++*launches;
     float* cur = b.Ab;
     float* nxt = b.Ab2;
-    for (int l = p.L - 1; l >= 0; --l) {
+    const int lstop = ab1 ? 1 : 0;
+    for (int l = p.L - 1; l >= lstop; --l) {
         LayerArgs la = layer_args(p, l, true);
         float* out = l == 0 ? g : nxt;
         const int ldo = p.ld[l];
@@ -332,15 +333,16 @@ cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
         ++*launches;
         float* t = cur; cur = out; nxt = t;
     }
+    if (ab1) *ab1 = cur;
     return cudaGetLastError();
 }
 
 cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N,
                            const float* wdot, const float* alpha_rows, float* dtheta, cudaStream_t s,
-                           int* launches)
+                           int* launches, bool tan_tc, const WgradTc* wtc)
 {
     // forward tangent along wdot: zdot_l = adot_{l-1} W_l^T, adot_l = act'(z_l) zdot_l
-    for (int l = 0; l < p.L; ++l) {
+    for (int l = tan_tc ? 1 : 0; l < p.L; ++l) {
         LayerArgs la = layer_args(p, l, false);
         const float* Ain = l == 0 ? wdot : b.Ad[l];
         k_gemm<true, PRO_NONE, EPI_TAN><<<gemm_grid(p, N, p.ld[l + 1]), 256, 0, s>>>(
@@ -360,11 +362,17 @@ cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
         LayerArgs lw = layer_args(p, l, false);
         const float* Ain = l == 0 ? b.G : b.A[l];
         const float* Adin = l == 0 ? wdot : b.Ad[l];
-        int kmax = 0, nmax = 0;
-        for (int q = 0; q < p.S; ++q) { kmax = max(kmax, lw.K[q]); nmax = max(nmax, lw.N[q]); }
-        dim3 gw((unsigned)((nmax + kBM - 1) / kBM), (unsigned)((kmax + 1 + kBN - 1) / kBN), (unsigned)(p.S * b.splits));
-        k_wgrad<<<gw, 256, 0, s>>>(lw, b.seg_off, b.splits, b.Zb, Ain, ldl, p.ld[l], b.Zdb, Adin, b.part, p.P);
-        ++*launches;
+        if (wtc && wtc->ws) {
+            cudaError_t e = tf32_wgrad(p, b, N, wtc->ws, wtc->mask, l, Ain, Adin, dtheta, wtc->status, s, launches);
+            if (e != cudaSuccess) return e;
+        } else {
+            int kmax = 0, nmax = 0;
+            for (int q = 0; q < p.S; ++q) { kmax = max(kmax, lw.K[q]); nmax = max(nmax, lw.N[q]); }
+            dim3 gw((unsigned)((nmax + kBM - 1) / kBM), (unsigned)((kmax + 1 + kBN - 1) / kBN),
+                    (unsigned)(p.S * b.splits));
+            k_wgrad<<<gw, 256, 0, s>>>(lw, b.seg_off, b.splits, b.Zb, Ain, ldl, p.ld[l], b.Zdb, Adin, b.part, p.P);
+            ++*launches;
+        }
         if (l > 0) {
             // abar_{l} = Zb W_{l+1}, adotbar_{l} = Zdb W_{l+1}
             LayerArgs la = layer_args(p, l, true);
@@ -375,8 +383,10 @@ cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
             *launches += 2;
         }
     }
-    k_reduce_splits<<<(unsigned)((p.P + 255) / 256), 256, 0, s>>>(p.P, b.splits, b.part, dtheta);
-    ++*launches;
+    if (!(wtc && wtc->ws)) {
+        k_reduce_splits<<<(unsigned)((p.P + 255) / 256), 256, 0, s>>>(p.P, b.splits, b.part, dtheta);
+        ++*launches;
+    }
     return cudaGetLastError();
 }
 

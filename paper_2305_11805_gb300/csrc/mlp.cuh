@@ -42,16 +42,47 @@ struct MlpBuffers {
 };
 
 cudaError_t mlp_tiles(const MlpPlan& p, const int32_t* seg_off, int32_t* tile_start, cudaStream_t s, int* launches);
-cudaError_t mlp_forward(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, cudaStream_t s, int* launches);
+// layers l0 .. L-1 (l0 = 1 when the first layer ran on the tensor cores)
+cudaError_t mlp_forward(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, cudaStream_t s, int* launches,
+                        int l0 = 0);
 cudaError_t mlp_energy_rows(const MlpPlan& p, const MlpBuffers& b, int64_t N, float* E_rows, cudaStream_t s, int* launches);
+// g = dE/dG; with ab1 != nullptr the chain stops at dE/dA_1 (row stride ld[1]), returned in *ab1
 cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, float* g,
-                           cudaStream_t s, int* launches);
+                           cudaStream_t s, int* launches, float** ab1 = nullptr);
 // BF16 tensor-core networks (mlp_tc.cu): energies and input gradients; ws from tc_workspace_bytes
 size_t tc_workspace_bytes(const MlpPlan& p, int64_t N, bool split);
 cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, void* ws,
                                  bool split, float* E_rows, float* g, DevStatus* status, cudaStream_t s,
                                  int* launches);
+struct WgradTc;
+// tan_tc: the first layer's tangent ran on the tensor cores (tf32_tangent1); wtc (non-null
+// ws): every layer's weight gradient on the tensor cores (tf32_wgrad)
 cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, const float* wdot,
-                           const float* alpha_rows, float* dtheta, cudaStream_t s, int* launches);
+                           const float* alpha_rows, float* dtheta, cudaStream_t s, int* launches,
+                           bool tan_tc = false, const WgradTc* wtc = nullptr);
+
+// FP32 networks with the first layer on the tensor cores as TF32 hi + lo pairs (mlp_tc.cu).
+// Order per call: tf32_prepare, tf32_forward1, mlp_forward(l0 = 1); mlp_input_grad(ab1) and
+// tf32_input_grad1; for training tf32_tangent1, then mlp_param_grad(tan_tc, wtc), which calls
+// tf32_wgrad for every layer.
+// Each of the four products may also stay on the CUDA cores (TF32_* bits below).
+enum { TF32_FWD = 1, TF32_INGRAD = 2, TF32_TAN = 4, TF32_WGRAD = 8 };
+bool tf32_first_layer_ok(const MlpPlan& p);
+// mask: the TF32_* products used in this evaluation (the same value in every call of one evaluation)
+size_t tf32_workspace_bytes(const MlpPlan& p, int64_t N, int mask);
+cudaError_t tf32_prepare(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, void* ws, int mask,
+                         cudaStream_t s, int* launches);
+cudaError_t tf32_forward1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, DevStatus* status,
+                          cudaStream_t s, int* launches);
+cudaError_t tf32_input_grad1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, const float* Ab1,
+                             float* g, DevStatus* status, cudaStream_t s, int* launches);
+cudaError_t tf32_tangent1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, const float* Gdot,
+                          DevStatus* status, cudaStream_t s, int* launches);
+// weight gradient of layer l+1 from b.Zb, b.Zdb (its adjoints) and its inputs A, Ad
+cudaError_t tf32_wgrad(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, int l, const float* A,
+                       const float* Ad, float* dtheta, DevStatus* status, cudaStream_t s, int* launches);
+
+// context of the tensor-core weight gradients inside mlp_param_grad (null ws: CUDA cores)
+struct WgradTc { void* ws; int mask; DevStatus* status; };
 
 }  // namespace panna

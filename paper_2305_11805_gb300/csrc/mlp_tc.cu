@@ -1,16 +1,22 @@
-// Per-species networks (Eq. 1) on the 5th-generation tensor cores: BF16 operands, FP32
-// accumulation in tensor memory (TMEM), operands staged by TMA.
+// Per-species networks (Eq. 1) on the 5th-generation tensor cores: BF16 or TF32 operands,
+// FP32 accumulation in tensor memory (TMEM), operands staged by TMA.  Either operand type
+// may be carried as a hi + lo pair (three MMAs per product, hi*hi + hi*lo + lo*hi): BF16
+// pairs keep about 16 significant bits, TF32 pairs about 22 (FP32-class results).
 //
 // One GEMM kernel, C[rows, N] = A[rows, K] B_s[N, K]^T, serves every layer:
 //   forward  Z_{l+1} = A_l W_l^T (+ b_l), A_{l+1} = act(Z_{l+1})       (B = W_l, K-major)
 //   backward abar_l  = zbar_{l+1} W_l,   zbar_l = abar_l * act'(Z_l)    (B = W_l^T, K-major)
 //            g       = zbar_1 W_0  (input gradient dE/dG, FP32 out)
+//   tangent  zdot_1  = Gdot W_0^T, adot_1 = act'(Z_1) zdot_1             (FP32 out)
+//   weights  dW_0    = zbar_1^T G + zdotbar_1^T Gdot  (sum over atoms: operands transposed
+//            so that atoms run along K, each species padded to 32 atoms; one CTA per
+//            (species, chunk of atoms, 128 outputs, N tile), partial sums reduced in order)
 // Rows are atoms in species order; a CTA owns one 128-row tile of one species (tile
 // table on the device) and one N tile of up to 256 columns.
 //
 // CTA of 6 warps: warp 0 issues TMA loads into a 4-stage ring (mbarrier full/empty),
 // warp 1 owns the TMEM allocation and one lane issues tcgen05.mma (M = 128, N = BN,
-// K = 16 per instruction, 4 per 64-wide K chunk) and tcgen05.commit; warps 2..5 read the
+// K = 16 BF16 or 8 TF32 per instruction, 4 per 128-byte K chunk) and tcgen05.commit; warps 2..5 read the
 // accumulator with tcgen05.ld (each warp its 32-lane quarter) and run the epilogue.
 // Every wait is bounded: on time-out the CTA sets PANNA_ERR_TIMEOUT, drains what it
 // issued, frees its TMEM and returns.
@@ -18,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
+#include <algorithm>
 #include <string.h>
 
 #include "mlp.cuh"
@@ -26,26 +33,35 @@ namespace panna {
 
 namespace {
 
-constexpr int kTcBM = 128, kTcBK = 64;
+constexpr int kTcBM = 128, kTcBK = 64;   // kTcBK: BF16 elements per 128-byte K chunk (32 for TF32)
 constexpr int kTcThreads = 192;
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kSpinLimit = 1ll << 25;
 constexpr uint32_t kTileA = kTcBM * kTcBK * 2;           // 16 KiB: one 128 x 64 BF16 tile
 
-// Pipeline geometry.  Plain: one BF16 copy of each operand, N tile up to 256, 4 stages.
-// Split (hi + lo BF16 pairs, three MMAs per K step): N tile up to 128, 3 stages.
-template <bool SPLIT>
+// Pipeline geometry by the number of parts each operand is carried in:
+//   1: plain, N tile up to 256, 4 stages;
+//   2: hi + lo (three MMAs per K step), N tile up to 128, 3 stages;
+//   3: hi + mid + lo, an exact split of FP32 into TF32 (six MMAs per K step: every cross term
+//      above 2^-32 of the product), N tile up to 128, 2 stages.
+template <int PARTS>
 struct TcCfg {
-    static constexpr int kMaxBN = SPLIT ? 128 : 256;
-    static constexpr int kStages = SPLIT ? 3 : 4;
-    static constexpr int kParts = SPLIT ? 2 : 1;
+    static constexpr int kMaxBN = PARTS == 1 ? 256 : 128;
+    static constexpr int kStages = PARTS == 1 ? 4 : (PARTS == 2 ? 3 : 2);
+    static constexpr int kParts = PARTS;
     static constexpr uint32_t kStageA = kParts * kTileA;
     static constexpr uint32_t kTileB = kMaxBN * kTcBK * 2;
     static constexpr uint32_t kStageB = kParts * kTileB;
     static constexpr size_t kSmem = 1024 + kStages * (kStageA + kStageB) + 256;
 };
 
-enum { TC_FWD = 1, TC_BWD_MID = 2, TC_BWD_OUT = 3 };
+enum { TC_FWD = 1, TC_BWD_MID = 2, TC_BWD_OUT = 3, TC_FWD32 = 4, TC_TAN32 = 5, TC_WGRAD = 6 };
+
+// TMA descriptors of the parts of both operands (one kernel parameter in param space)
+struct TcMaps {
+    CUtensorMap a[3];
+    CUtensorMap b[3];
+};
 
 struct TcArgs {
     int S;
@@ -58,7 +74,15 @@ struct TcArgs {
     float* outF; int ldF;      // FWD: Z (FP32); BWD_OUT: g (FP32)
     __nv_bfloat16* outH; int ldH;  // FWD: act(Z); BWD_MID: zbar (BF16, hi part when split)
     __nv_bfloat16* outL;           // split: lo part, same layout as outH
-    const float* Zin; int ldZ;     // BWD_MID: Z for act'
+    const float* Zin; int ldZ;     // BWD_MID, TAN32: Z for act'
+    float* outA; int ldA;          // FWD32: act(Z); TAN32: act'(Z) zdot (FP32)
+    // WGRAD: species-padded transposed operands, items = (species, chunk of atoms)
+    const int32_t* item_start;     // [S+1]
+    const int32_t* pstart;         // [S+1] padded column of each species' first atom
+    int Kp;                        // column offset of the second product's operands
+    int chunk;                     // atoms per item (multiple of 32)
+    float* part; int ldn;          // part[(item * Mvalid + m) * ldn + n]
+    int Mvalid, Nvalid;            // outputs m < Mvalid, n < Nvalid
     const int32_t* seg_off;
     const int32_t* tile_start;
     DevStatus* status;
@@ -121,12 +145,19 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+template <bool TF>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
 {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                 ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-                 : "memory");
+    if (TF)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                     ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                     : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                     ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                     : "memory");
 }
 
 __device__ __forceinline__ void tc_commit(uint64_t* bar)
@@ -162,11 +193,38 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M x N.
-__device__ __forceinline__ uint32_t idesc_bf16(uint32_t M, uint32_t N)
+// Instruction descriptor: D FP32, A and B both K-major, M x N; operand format BF16
+// (kind::f16, code 1) or TF32 (kind::tf32, code 2).
+__device__ __forceinline__ uint32_t idesc_mma(bool tf32, uint32_t M, uint32_t N)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+    const uint32_t fmt = tf32 ? 2u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
+
+// x rounded to TF32 (10 explicit mantissa bits, low 13 bits of the FP32 pattern zero)
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// v as up to three TF32 parts: hi = tf32(v), mid = tf32(v - hi), lo = v - hi - mid.  Each
+// difference is exact in FP32, and the three parts add up to v exactly (11 + 11 + at most
+// 3 significant bits).  Parts whose pointer is null are not written.
+__device__ __forceinline__ void store_split_tf32(float* hi, float* mid, float* lo, size_t idx, float v)
+{
+    const float h = to_tf32(v);
+    hi[idx] = h;
+    if (mid) {
+        const float r = v - h;
+        const float m = to_tf32(r);
+        mid[idx] = m;
+        if (lo) lo[idx] = to_tf32(r - m);
+    }
+}
+
+struct Parts3 { float* p[3]; };   // destinations of up to three TF32 parts (null = not written)
 
 __device__ __forceinline__ float act_f(int t, float z)
 {
@@ -194,17 +252,18 @@ __device__ __forceinline__ void store_split(__nv_bfloat16* hi, __nv_bfloat16* lo
     if (lo) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-template <int EPI, bool SPLIT>
+template <int EPI, int PARTS, bool TF>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, TcArgs a)
+k_tc_gemm(const __grid_constant__ TcMaps tm, TcArgs a)
 {
-    using Cfg = TcCfg<SPLIT>;
+    using Cfg = TcCfg<PARTS>;
     constexpr int kStages = Cfg::kStages;
+    constexpr int BKE = TF ? kTcBK / 2 : kTcBK;          // elements per 128-byte K chunk
+    constexpr int MMAK = TF ? 8 : 16;                    // K per instruction (32 bytes)
     extern __shared__ unsigned char smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = smem;                                  // [stage][part] 128 x 64 tiles
-    uint8_t* sB = smem + kStages * Cfg::kStageA;         // [stage][part] BN x 64 tiles
+    uint8_t* sA = smem;                                  // [stage][part] 128 x 128 B tiles
+    uint8_t* sB = smem + kStages * Cfg::kStageA;         // [stage][part] BN x 128 B tiles
     uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * Cfg::kStageB);
     uint64_t* empty = full + kStages;
     uint64_t* accf = empty + kStages;
@@ -212,15 +271,29 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x;
-    if (tile >= a.tile_start[a.S]) return;              // whole CTA: no barrier touched yet
-    int s = 0;
-    while (tile >= a.tile_start[s + 1]) ++s;
-    const int n0 = blockIdx.y * a.BN;
-    if (n0 >= a.N[s]) return;
-    const int row0 = a.seg_off[s] + (tile - a.tile_start[s]) * kTcBM;
-    const int rend = a.seg_off[s + 1];
-    const int nk = (a.K + kTcBK - 1) / kTcBK;
+    // work decode (whole-CTA returns happen before any barrier or TMEM use)
+    int s = 0, row0 = 0, rend = 0, n0 = 0, m0 = 0, kbeg = 0, nkh = 0, nk = 0;
+    const int item = blockIdx.x;
+    if (EPI == TC_WGRAD) {
+        if (item >= a.item_start[a.S]) return;
+        while (item >= a.item_start[s + 1]) ++s;
+        kbeg = a.pstart[s] + (item - a.item_start[s]) * a.chunk;
+        const int kend = min(kbeg + a.chunk, a.pstart[s + 1]);
+        nkh = (kend - kbeg) / BKE;
+        nk = 2 * nkh;                                     // first product, then the second
+        n0 = blockIdx.y * a.BN;
+        m0 = blockIdx.z * kTcBM;
+        if (nk == 0 || n0 >= a.Nvalid || m0 >= a.Mvalid) return;
+    } else {
+        const int tile = blockIdx.x;
+        if (tile >= a.tile_start[a.S]) return;
+        while (tile >= a.tile_start[s + 1]) ++s;
+        n0 = blockIdx.y * a.BN;
+        if (n0 >= a.N[s]) return;
+        row0 = a.seg_off[s] + (tile - a.tile_start[s]) * kTcBM;
+        rend = a.seg_off[s + 1];
+        nk = (a.K + BKE - 1) / BKE;
+    }
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) { mbar_init(full + i, 1); mbar_init(empty + i, 1); }
@@ -233,7 +306,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t bytes = Cfg::kParts * (kTileA + (uint32_t)a.BN * kTcBK * 2);
+    const uint32_t bytes = Cfg::kParts * (kTileA + (uint32_t)a.BN * 128u);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -245,11 +318,20 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 mbar_expect_tx(full + st, bytes);
                 uint8_t* a_st = sA + st * Cfg::kStageA;
                 uint8_t* b_st = sB + st * Cfg::kStageB;
-                tma_load_2d(a_st, &tmA, kc * kTcBK, row0, full + st);
-                tma_load_2d(b_st, &tmB, kc * kTcBK, s * a.n_pad + n0, full + st);
-                if (SPLIT) {
-                    tma_load_2d(a_st + kTileA, &tmA2, kc * kTcBK, row0, full + st);
-                    tma_load_2d(b_st + Cfg::kTileB, &tmB2, kc * kTcBK, s * a.n_pad + n0, full + st);
+                int ka, ra, kb, rb;
+                if (EPI == TC_WGRAD) {
+                    ka = kb = kc < nkh ? kbeg + kc * BKE : a.Kp + kbeg + (kc - nkh) * BKE;
+                    ra = m0;
+                    rb = n0;
+                } else {
+                    ka = kb = kc * BKE;
+                    ra = row0;
+                    rb = s * a.n_pad + n0;
+                }
+#pragma unroll
+                for (int q = 0; q < PARTS; ++q) {
+                    tma_load_2d(a_st + q * kTileA, &tm.a[q], ka, ra, full + st);
+                    tma_load_2d(b_st + q * Cfg::kTileB, &tm.b[q], kb, rb, full + st);
                 }
                 ++issued;
             }
@@ -259,7 +341,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(kTcBM, (uint32_t)a.BN);
+            const uint32_t idesc = idesc_mma(TF, kTcBM, (uint32_t)a.BN);
             bool ok = true;
             for (int kc = 0; kc < nk; ++kc) {
                 const int st = kc % kStages;
@@ -268,13 +350,22 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(sA + st * Cfg::kStageA), b0 = smem_u32(sB + st * Cfg::kStageB);
 #pragma unroll
-                for (int kk = 0; kk < kTcBK / 16; ++kk) {
-                    const uint64_t ah = sw128_desc(a0 + kk * 32), bh = sw128_desc(b0 + kk * 32);
-                    tc_mma(tmem, ah, bh, idesc, (kc | kk) ? 1u : 0u);
-                    if (SPLIT) {
-                        // hi*lo and lo*hi terms; lo*lo is below the accumulation precision
-                        tc_mma(tmem, ah, sw128_desc(b0 + Cfg::kTileB + kk * 32), idesc, 1u);
-                        tc_mma(tmem, sw128_desc(a0 + kTileA + kk * 32), bh, idesc, 1u);
+                for (int kk = 0; kk < BKE / MMAK; ++kk) {
+                    const uint64_t a1 = sw128_desc(a0 + kk * 32), b1 = sw128_desc(b0 + kk * 32);
+                    tc_mma<TF>(tmem, a1, b1, idesc, (kc | kk) ? 1u : 0u);
+                    if (PARTS >= 2) {
+                        // cross terms down to 2^-22 (two parts) or 2^-33 (three parts) of the product
+                        const uint64_t a2 = sw128_desc(a0 + kTileA + kk * 32);
+                        const uint64_t b2 = sw128_desc(b0 + Cfg::kTileB + kk * 32);
+                        tc_mma<TF>(tmem, a1, b2, idesc, 1u);
+                        tc_mma<TF>(tmem, a2, b1, idesc, 1u);
+                        if (PARTS >= 3) {
+                            const uint64_t a3 = sw128_desc(a0 + 2 * kTileA + kk * 32);
+                            const uint64_t b3 = sw128_desc(b0 + 2 * Cfg::kTileB + kk * 32);
+                            tc_mma<TF>(tmem, a1, b3, idesc, 1u);
+                            tc_mma<TF>(tmem, a2, b2, idesc, 1u);
+                            tc_mma<TF>(tmem, a3, b1, idesc, 1u);
+                        }
                     }
                 }
                 tc_commit(empty + st);
@@ -284,14 +375,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         }
     } else {
         const int q = warp & 3;                    // TMEM lane quarter of this warp
-        const int r = row0 + q * 32 + lane;        // this thread's row
+        const int r = row0 + q * 32 + lane;        // this thread's row (WGRAD: output m)
+        const int m = m0 + q * 32 + lane;
         if (mbar_wait(accf, 0, abort_flag)) {
             tc_fence_after();
-            const int Ns = a.N[s];
+            const int Ns = EPI == TC_WGRAD ? a.Nvalid : a.N[s];
             for (int c0 = 0; c0 < a.BN; c0 += 16) {
                 float v[16];
                 tc_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                if (r >= rend) continue;
+                if (EPI == TC_WGRAD ? m >= a.Mvalid : r >= rend) continue;
                 const int nb = n0 + c0;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -300,10 +392,19 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     if (EPI == TC_FWD) {
                         const float z = v[j] + a.bias[s * a.n_pad + n];
                         a.outF[(size_t)r * a.ldF + n] = z;
-                        store_split(a.outH, SPLIT ? a.outL : nullptr, (size_t)r * a.ldH + n, act_f(a.act[s], z));
+                        store_split(a.outH, PARTS >= 2 ? a.outL : nullptr, (size_t)r * a.ldH + n, act_f(a.act[s], z));
                     } else if (EPI == TC_BWD_MID) {
                         const float zb = v[j] * act_d1(a.act[s], a.Zin[(size_t)r * a.ldZ + n]);
-                        store_split(a.outH, SPLIT ? a.outL : nullptr, (size_t)r * a.ldH + n, zb);
+                        store_split(a.outH, PARTS >= 2 ? a.outL : nullptr, (size_t)r * a.ldH + n, zb);
+                    } else if (EPI == TC_FWD32) {
+                        const float z = v[j] + a.bias[s * a.n_pad + n];
+                        a.outF[(size_t)r * a.ldF + n] = z;
+                        a.outA[(size_t)r * a.ldA + n] = act_f(a.act[s], z);
+                    } else if (EPI == TC_TAN32) {
+                        a.outF[(size_t)r * a.ldF + n] = v[j];
+                        a.outA[(size_t)r * a.ldA + n] = act_d1(a.act[s], a.Zin[(size_t)r * a.ldZ + n]) * v[j];
+                    } else if (EPI == TC_WGRAD) {
+                        a.part[((size_t)item * a.Mvalid + m) * a.ldn + n] = v[j];
                     } else {
                         a.outF[(size_t)r * a.ldF + n] = v[j];
                     }
@@ -315,7 +416,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0 && *abort_flag) set_status(a.status, PANNA_ERR_TIMEOUT, tile);
+    if (threadIdx.x == 0 && *abort_flag) set_status(a.status, PANNA_ERR_TIMEOUT, blockIdx.x);
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
@@ -344,11 +445,123 @@ __global__ void k_to_bf16(int64_t n, const float* __restrict__ x, __nv_bfloat16*
     if (i < n) store_split(hi, lo, i, x[i]);
 }
 
-// Stacked BF16 weights of layer l for all species:
+__device__ __forceinline__ void store_parts(__nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16*, size_t idx, float v)
+{
+    store_split(hi, lo, idx, v);
+}
+__device__ __forceinline__ void store_parts(float* hi, float* mid, float* lo, size_t idx, float v)
+{
+    store_split_tf32(hi, mid, lo, idx, v);
+}
+
+// rows x cols FP32 (row stride lds) -> TF32 parts (row stride ldo, zero padding columns)
+__global__ void k_split_tf32(int64_t rows, int cols, int lds, int ldo, const float* __restrict__ x, Parts3 o)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * ldo) return;
+    const int64_t r = i / ldo;
+    const int c = (int)(i % ldo);
+    store_split_tf32(o.p[0], o.p[1], o.p[2], (size_t)i, c < cols ? x[(size_t)r * lds + c] : 0.f);
+}
+
+// zbar_1 = abar_1 * act'(Z_1) as TF32 parts (row stride ldo); 0 outside the species' width
+// and on rows past the last species
+__global__ void k_dact_split_tf32(int64_t N, int ld, int ldo, LayerArgs la, const int32_t* __restrict__ seg_off,
+                                  const float* __restrict__ Ab, const float* __restrict__ Z, Parts3 o)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * ldo) return;
+    const int64_t r = i / ldo;
+    const int c = (int)(i % ldo);
+    float v = 0.f;
+    if (r < seg_off[la.S]) {
+        int s = 0;
+        while (s < la.S - 1 && r >= seg_off[s + 1]) ++s;
+        if (c < la.N[s]) v = Ab[(size_t)r * ld + c] * act_d1(la.act[s], Z[(size_t)r * ld + c]);
+    }
+    store_split_tf32(o.p[0], o.p[1], o.p[2], (size_t)i, v);
+}
+
+// Padded atom columns for the weight gradient: species s owns columns
+// pstart[s] .. pstart[s] + round_up(n_s, 32) - 1, cut into items of `chunk` columns.
+__global__ void k_tf32_items(int S, const int32_t* __restrict__ seg_off, int chunk, int32_t* __restrict__ pstart,
+                             int32_t* __restrict__ item_start)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int p = 0, it = 0;
+        for (int s = 0; s < S; ++s) {
+            pstart[s] = p;
+            item_start[s] = it;
+            const int len = (seg_off[s + 1] - seg_off[s] + 31) / 32 * 32;
+            p += len;
+            it += (len + chunk - 1) / chunk;
+        }
+        pstart[S] = p;
+        item_start[S] = it;
+    }
+}
+
+struct Widths { int n[kMaxSpecies]; };
+
+// Transposed TF32 pairs with atoms along columns:
+//   dst[f * ldT + col_off + pstart[s] + (r - seg_off[s])] = src[r * lds + f]  for f < width_s,
+// 1 in row f == ones_row (the bias input) for every atom, 0 elsewhere (padding atoms, f past
+// the species' width, rows up to frows).  One CTA moves a 32 x 32 tile through shared memory.
+__global__ void __launch_bounds__(256)
+k_transpose_split(const float* __restrict__ src, int lds, int S, const int32_t* __restrict__ seg_off,
+                  const int32_t* __restrict__ pstart, Widths w, int frows, int ones_row, Parts3 o, int64_t ldT,
+                  int64_t col_off)
+{
+    __shared__ float tile[32][33];
+    const int p0 = blockIdx.x * 32;
+    if (p0 >= pstart[S]) return;
+    int s = 0;
+    while (p0 >= pstart[s + 1]) ++s;
+    const int f0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int cnt = seg_off[s + 1] - seg_off[s];
+    for (int pp = ty; pp < 32; pp += 8) {
+        const int loc = p0 - pstart[s] + pp;
+        const int f = f0 + tx;
+        float v = 0.f;
+        if (loc < cnt) {
+            if (f < w.n[s]) v = src[(size_t)(seg_off[s] + loc) * lds + f];
+            else if (f == ones_row) v = 1.f;
+        }
+        tile[pp][tx] = v;
+    }
+    __syncthreads();
+    for (int ff = ty; ff < 32; ff += 8) {
+        const int f = f0 + ff;
+        if (f >= frows) break;
+        store_split_tf32(o.p[0], o.p[1], o.p[2], (size_t)f * ldT + col_off + p0 + tx, tile[tx][ff]);
+    }
+}
+
+// dtheta of one layer from the per-item partial sums, in item order (deterministic):
+// n < K_s: weight W[m][n]; n == ldn - 1 (the row of ones): bias b[m].
+__global__ void k_wgrad_reduce(LayerArgs la, const int32_t* __restrict__ item_start, int Mvalid, int ldn,
+                               const float* __restrict__ part, float* __restrict__ dtheta)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)la.S * Mvalid * ldn) return;
+    const int s = (int)(idx / ((int64_t)Mvalid * ldn));
+    const int m = (int)((idx / ldn) % Mvalid);
+    const int n = (int)(idx % ldn);
+    const int K = la.K[s];
+    if (m >= la.N[s] || (n >= K && n != ldn - 1)) return;
+    float acc = 0.f;
+    for (int it = item_start[s]; it < item_start[s + 1]; ++it) acc += part[((size_t)it * Mvalid + m) * ldn + n];
+    if (n < K) dtheta[la.w_off[s] + (int64_t)m * K + n] = acc;
+    else dtheta[la.b_off[s] + m] = acc;
+}
+
+// Stacked weights of layer l for all species (BF16 hi + lo or up to three TF32 parts):
 //   fwd: out[(s*npad + n) * kpad + k] = W_s[n][k]      (n < n_out_s, k < n_in_s, else 0)
 //   bwd: out[(s*npad + k) * kpad + n] = W_s[n][k]      (the transpose)
+template <typename T>
 __global__ void k_stack_weights(LayerArgs la, const float* __restrict__ theta, int npad, int kpad, int transpose,
-                                __nv_bfloat16* __restrict__ out, __nv_bfloat16* __restrict__ out_lo,
+                                T* __restrict__ out, T* __restrict__ out_lo, T* __restrict__ out_lo2,
                                 float* __restrict__ bias_out)
 {
     const int64_t total = (int64_t)la.S * npad * kpad;
@@ -361,7 +574,7 @@ __global__ void k_stack_weights(LayerArgs la, const float* __restrict__ theta, i
     const int n = transpose ? cc : rr, k = transpose ? rr : cc;
     float v = 0.f;
     if (n < n_out && k < n_in) v = theta[la.w_off[s] + (int64_t)n * n_in + k];
-    store_split(out, out_lo, idx, v);
+    store_parts(out, out_lo, out_lo2, idx, v);
     if (bias_out && !transpose && cc == 0) bias_out[(int64_t)s * npad + rr] = rr < n_out ? theta[la.b_off[s] + rr] : 0.f;
 }
 
@@ -412,15 +625,19 @@ cudaError_t get_encoder()
     return cudaSuccess;
 }
 
-// 2D BF16 tensor [rows x cols] (row stride ld elements), box [box_rows x 64], 128 B swizzle
-cudaError_t make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows)
+// 2D tensor [rows x cols] (row stride ld elements) of BF16 (box [box_rows x 64]) or FP32
+// holding TF32 values (box [box_rows x 32]): 128-byte rows, 128 B swizzle
+cudaError_t make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                     bool tf32 = false)
 {
-    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16) return cudaErrorInvalidValue;
+    const int64_t es = tf32 ? 4 : 2;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * es) % 16) return cudaErrorInvalidValue;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+    CUresult r = g_encode(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          const_cast<void*>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -445,21 +662,28 @@ LayerArgs tc_layer_args(const MlpPlan& p, int l)
 
 int tc_bn(int n, int max_bn) { int t = (n + max_bn - 1) / max_bn; return round_up((n + t - 1) / t, 16); }
 
-template <int EPI, bool SPLIT>
-cudaError_t launch_tc(const CUtensorMap* m, const TcArgs& ta, int64_t N, int nmax, cudaStream_t s)
+template <int EPI, int PARTS, bool TF = false>
+cudaError_t launch_tc_grid(const TcMaps& m, const TcArgs& ta, dim3 grid, cudaStream_t s)
 {
-    const int smem = (int)TcCfg<SPLIT>::kSmem;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<EPI, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = (int)TcCfg<PARTS>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<EPI, PARTS, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((N + kTcBM - 1) / kTcBM + ta.S), (unsigned)((nmax + ta.BN - 1) / ta.BN));
-    k_tc_gemm<EPI, SPLIT><<<grid, kTcThreads, smem, s>>>(m[0], m[1], m[2], m[3], ta);
+    k_tc_gemm<EPI, PARTS, TF><<<grid, kTcThreads, smem, s>>>(m, ta);
     return cudaGetLastError();
 }
 
-template <int EPI>
-cudaError_t launch_tc_any(bool split, const CUtensorMap* m, const TcArgs& ta, int64_t N, int nmax, cudaStream_t s)
+// row-tiled launch: one CTA per (species, 128-row tile) and N tile
+template <int EPI, int PARTS, bool TF = false>
+cudaError_t launch_tc(const TcMaps& m, const TcArgs& ta, int64_t N, int nmax, cudaStream_t s)
 {
-    return split ? launch_tc<EPI, true>(m, ta, N, nmax, s) : launch_tc<EPI, false>(m, ta, N, nmax, s);
+    dim3 grid((unsigned)((N + kTcBM - 1) / kTcBM + ta.S), (unsigned)((nmax + ta.BN - 1) / ta.BN));
+    return launch_tc_grid<EPI, PARTS, TF>(m, ta, grid, s);
+}
+
+template <int EPI>
+cudaError_t launch_tc_any(bool split, const TcMaps& m, const TcArgs& ta, int64_t N, int nmax, cudaStream_t s)
+{
+    return split ? launch_tc<EPI, 2>(m, ta, N, nmax, s) : launch_tc<EPI, 1>(m, ta, N, nmax, s);
 }
 
 // Buffers of the BF16 networks, carved from one workspace block (sizing when base == nullptr).
@@ -484,7 +708,7 @@ size_t tc_carve(const MlpPlan& p, int64_t N, bool split, char* base, TcBufs& t)
         return q;
     };
     const int parts = split ? 2 : 1;
-    const int max_bn = split ? TcCfg<true>::kMaxBN : TcCfg<false>::kMaxBN;
+    const int max_bn = split ? TcCfg<2>::kMaxBN : TcCfg<1>::kMaxBN;
     t.tiles128 = static_cast<int32_t*>(take((kMaxSpecies + 1) * sizeof(int32_t)));
     t.ldh[0] = round_up(p.ld[0], 8);
     for (int q = 0; q < 2; ++q) t.G16[q] = q < parts ? static_cast<__nv_bfloat16*>(take((size_t)N * t.ldh[0] * 2)) : nullptr;
@@ -549,11 +773,11 @@ cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const fl
         const int no = p.ld[l + 1], ni = p.ld[l];
         LayerArgs la = tc_layer_args(p, l);
         int64_t tf = (int64_t)p.S * t.npf[l] * round_up(ni, 8);
-        k_stack_weights<<<(unsigned)((tf + 255) / 256), 256, 0, s>>>(la, theta, t.npf[l], round_up(ni, 8), 0,
-                                                                    t.Wf[l][0], t.Wf[l][1], t.bias[l]);
+        k_stack_weights<__nv_bfloat16><<<(unsigned)((tf + 255) / 256), 256, 0, s>>>(la, theta, t.npf[l], round_up(ni, 8), 0,
+                                                                    t.Wf[l][0], t.Wf[l][1], nullptr, t.bias[l]);
         int64_t tb = (int64_t)p.S * t.npb[l] * round_up(no, 8);
-        k_stack_weights<<<(unsigned)((tb + 255) / 256), 256, 0, s>>>(la, theta, t.npb[l], round_up(no, 8), 1,
-                                                                    t.Wb[l][0], t.Wb[l][1], nullptr);
+        k_stack_weights<__nv_bfloat16><<<(unsigned)((tb + 255) / 256), 256, 0, s>>>(la, theta, t.npb[l], round_up(no, 8), 1,
+                                                                    t.Wb[l][0], t.Wb[l][1], nullptr, nullptr);
         *launches += 2;
     }
     // padding columns of the BF16 operands meet zero weights, but must not hold NaN
@@ -571,7 +795,7 @@ cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const fl
     base.seg_off = b.seg_off;
     base.tile_start = t.tiles128;
     base.status = status;
-    CUtensorMap maps[4];   // A hi, B hi, A lo, B lo
+    TcMaps maps;
     // forward through the hidden layers
     for (int l = 0; l < p.L - 1; ++l) {
         CUtensorMap mA[2], mB[2];
@@ -580,7 +804,7 @@ cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const fl
         if (e == cudaSuccess)
             e = make_maps(mB, t.Wf[l], parts, (int64_t)p.S * t.npf[l], p.ld[l], round_up(p.ld[l], 8), t.bnf[l]);
         if (e != cudaSuccess) return e;
-        maps[0] = mA[0]; maps[1] = mB[0]; maps[2] = mA[1]; maps[3] = mB[1];
+        maps.a[0] = mA[0]; maps.b[0] = mB[0]; maps.a[1] = mA[1]; maps.b[1] = mB[1];
         TcArgs ta = base;
         for (int q = 0; q < p.S; ++q) { ta.N[q] = p.widths[q][l + 1]; ta.act[q] = p.acts[q][l]; }
         ta.K = p.ld[l];
@@ -610,7 +834,7 @@ cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const fl
             e = make_maps(mB, t.Wb[l], parts, (int64_t)p.S * t.npb[l], p.ld[l + 1], round_up(p.ld[l + 1], 8),
                           t.bnb[l]);
         if (e != cudaSuccess) return e;
-        maps[0] = mA[0]; maps[1] = mB[0]; maps[2] = mA[1]; maps[3] = mB[1];
+        maps.a[0] = mA[0]; maps.b[0] = mB[0]; maps.a[1] = mA[1]; maps.b[1] = mB[1];
         TcArgs ta = base;
         for (int q = 0; q < p.S; ++q) ta.N[q] = p.widths[q][l];
         ta.K = p.ld[l + 1];
@@ -628,6 +852,258 @@ cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const fl
         if (e != cudaSuccess) return e;
         ++*launches;
     }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP32 networks, first layer on TF32 pairs
+//
+// The first layer (descriptor width D -> first hidden width) carries almost all of the
+// networks' arithmetic.  With FP32 networks it runs on the tensor cores as TF32 hi + lo
+// pairs (three MMAs per product, about 22 significant bits per operand); the narrow deeper
+// layers stay on the CUDA-core kernels of mlp.cu.
+
+namespace {
+
+// Parts per operand: three (exact splits of FP32, products exact to 2^-32) for the forward
+// and input-gradient products, two in the training-only products (tangent, weight
+// gradient).  The accumulation inside the MMA, not the operand split, then limits the
+// accuracy: its error grows with the length of the K chain about linearly (a CUDA-core
+// FP32 chain rounds to nearest and grows about as its square root), so the forward
+// product, whose error reaches the forces through act' and act'', stays on the CUDA cores
+// unless TF32_FWD is asked for.
+constexpr int kPartsFwd = 3, kPartsTan = 2, kPartsW = 2;
+
+struct Tf32Bufs {
+    int32_t* tiles128;
+    int32_t* pstart;
+    int32_t* items;
+    float* Wf[3];          // [S * npf, kpf]   W_1, K-major over D
+    float* Wb[3];          // [S * npb, kpb]   W_1^T, K-major over the first hidden width
+    float* bias;           // [S * npf]
+    float* G[3];           // [N, D]           descriptors (forward), then their tangent (training)
+    float* Zb[3];          // [N, ldz]         zbar_1 of the input gradient
+    float* ZT[3];          // [max width, 2 Kp]  zbar_l | zdotbar_l, atoms along columns (2 parts)
+    float* GT[3];          // [max input + 1, 2 Kp]  A_{l-1} (+ a row of ones) | Adot_{l-1}, likewise
+    float* part;           // [items, max over layers of ld[l+1] (ld[l] + 1)]
+    int npf, npb, bnf, bnb, bnw, kpf, kpb, ldz, chunk, items_max;
+    int64_t Kp;
+};
+
+// buffers of the products in `mask` (TF32_* bits) only
+size_t tf32_carve(const MlpPlan& p, int64_t N, int mask, char* base, Tf32Bufs& t)
+{
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        void* q = base ? base + off : nullptr;
+        off += (n + 255) & ~(size_t)255;
+        return q;
+    };
+    const int D = p.ld[0], h1 = p.ld[1], S = p.S;
+    const int maxbn = TcCfg<kPartsFwd>::kMaxBN;
+    t.bnf = tc_bn(h1, maxbn); t.npf = round_up(h1, t.bnf); t.kpf = round_up(D, 4);
+    t.bnb = tc_bn(D, maxbn); t.npb = round_up(D, t.bnb); t.kpb = round_up(h1, 4);
+    t.bnw = tc_bn(D + 1, TcCfg<kPartsW>::kMaxBN);
+    t.ldz = round_up(h1, 4);
+    t.Kp = (N + 31) / 32 * 32 + 32 * (int64_t)S;
+    t.chunk = (int)std::max<int64_t>(512, (N / 256 + 31) / 32 * 32);
+    t.items_max = (int)((t.Kp + t.chunk - 1) / t.chunk) + S;
+    t.tiles128 = static_cast<int32_t*>(take((kMaxSpecies + 1) * sizeof(int32_t)));
+    t.pstart = static_cast<int32_t*>(take((kMaxSpecies + 1) * sizeof(int32_t)));
+    t.items = static_cast<int32_t*>(take((kMaxSpecies + 1) * sizeof(int32_t)));
+    const int pf = (mask & TF32_FWD) ? kPartsFwd : ((mask & TF32_TAN) ? kPartsTan : 0);   // W_1 and G parts
+    const int pb = (mask & TF32_INGRAD) ? kPartsFwd : 0;
+    const int pw = (mask & TF32_WGRAD) ? kPartsW : 0;
+    int in_max = 0;   // widest layer input (rows of the transposed inputs, plus the row of ones)
+    for (int l = 0; l < p.L; ++l) in_max = std::max(in_max, p.ld[l]);
+    for (int q = 0; q < 3; ++q) {
+        t.Wf[q] = q < pf ? static_cast<float*>(take((size_t)S * t.npf * t.kpf * 4)) : nullptr;
+        t.G[q] = q < pf ? static_cast<float*>(take((size_t)N * D * 4)) : nullptr;
+        t.Wb[q] = q < pb ? static_cast<float*>(take((size_t)S * t.npb * t.kpb * 4)) : nullptr;
+        t.Zb[q] = q < pb ? static_cast<float*>(take((size_t)N * t.ldz * 4)) : nullptr;
+        t.ZT[q] = q < pw ? static_cast<float*>(take((size_t)p.max_hidden * 2 * t.Kp * 4)) : nullptr;
+        t.GT[q] = q < pw ? static_cast<float*>(take((size_t)(in_max + 1) * 2 * t.Kp * 4)) : nullptr;
+    }
+    t.bias = static_cast<float*>(take((size_t)S * t.npf * 4));
+    size_t part_max = 0;
+    for (int l = 0; l < p.L; ++l) part_max = std::max(part_max, (size_t)p.ld[l + 1] * (p.ld[l] + 1));
+    t.part = pw ? static_cast<float*>(take((size_t)t.items_max * part_max * 4)) : nullptr;
+    return off + 4096;
+}
+
+Parts3 parts_of(float* const* b, int parts)
+{
+    Parts3 o{};
+    for (int q = 0; q < parts; ++q) o.p[q] = b[q];
+    return o;
+}
+
+cudaError_t tf32_maps(TcMaps& m, int parts, float* const* a, int64_t arows, int64_t acols, int64_t alda, int abox,
+                      float* const* b, int64_t brows, int64_t bcols, int64_t bldb, int bbox)
+{
+    for (int q = 0; q < parts; ++q) {
+        cudaError_t e = make_map(&m.a[q], a[q], arows, acols, alda, abox, true);
+        if (e == cudaSuccess) e = make_map(&m.b[q], b[q], brows, bcols, bldb, bbox, true);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+TcArgs tf32_base(const MlpPlan& p, const MlpBuffers& b, const Tf32Bufs& t, DevStatus* status)
+{
+    TcArgs ta{};
+    ta.S = p.S;
+    ta.seg_off = b.seg_off;
+    ta.tile_start = t.tiles128;
+    ta.status = status;
+    return ta;
+}
+
+unsigned blocks(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+bool tf32_first_layer_ok(const MlpPlan& p) { return p.L >= 2 && p.ld[0] % 4 == 0; }
+
+size_t tf32_workspace_bytes(const MlpPlan& p, int64_t N, int mask)
+{
+    Tf32Bufs t;
+    return tf32_carve(p, N, mask, nullptr, t);
+}
+
+cudaError_t tf32_prepare(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, void* ws, int mask,
+                         cudaStream_t s, int* launches)
+{
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    Tf32Bufs t;
+    tf32_carve(p, N, mask, static_cast<char*>(ws), t);
+    k_tiles128<<<1, 32, 0, s>>>(p.S, b.seg_off, t.tiles128);
+    ++*launches;
+    LayerArgs la = tc_layer_args(p, 0);
+    if (t.Wf[0]) {
+        k_stack_weights<float><<<blocks((int64_t)p.S * t.npf * t.kpf), 256, 0, s>>>(la, theta, t.npf, t.kpf, 0, t.Wf[0],
+                                                                                   t.Wf[1], t.Wf[2], t.bias);
+        ++*launches;
+    }
+    if (t.Wb[0]) {
+        k_stack_weights<float><<<blocks((int64_t)p.S * t.npb * t.kpb), 256, 0, s>>>(la, theta, t.npb, t.kpb, 1, t.Wb[0],
+                                                                                   t.Wb[1], t.Wb[2], nullptr);
+        ++*launches;
+    }
+    if (mask & TF32_WGRAD) {
+        k_tf32_items<<<1, 32, 0, s>>>(p.S, b.seg_off, t.chunk, t.pstart, t.items);
+        ++*launches;
+    }
+    return cudaGetLastError();
+}
+
+// Z_1 = G W_1^T + b_1, A_1 = act(Z_1) (FP32 out)
+cudaError_t tf32_forward1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, DevStatus* status,
+                          cudaStream_t s, int* launches)
+{
+    Tf32Bufs t;
+    tf32_carve(p, N, mask, static_cast<char*>(ws), t);
+    const int D = p.ld[0];
+    k_split_tf32<<<blocks(N * D), 256, 0, s>>>(N, D, D, D, b.G, parts_of(t.G, kPartsFwd));
+    ++*launches;
+    TcMaps m;
+    cudaError_t e = tf32_maps(m, kPartsFwd, t.G, N, D, D, kTcBM, t.Wf, (int64_t)p.S * t.npf, D, t.kpf, t.bnf);
+    if (e != cudaSuccess) return e;
+    TcArgs ta = tf32_base(p, b, t, status);
+    for (int q = 0; q < p.S; ++q) { ta.N[q] = p.widths[q][1]; ta.act[q] = p.acts[q][0]; }
+    ta.K = D; ta.BN = t.bnf; ta.n_pad = t.npf; ta.bias = t.bias;
+    ta.outF = b.Z[1]; ta.ldF = p.ld[1];
+    ta.outA = b.A[1]; ta.ldA = p.ld[1];
+    e = launch_tc<TC_FWD32, kPartsFwd, true>(m, ta, N, p.ld[1], s);
+    ++*launches;
+    return e;
+}
+
+// g = (abar_1 * act'(Z_1)) W_1 (FP32 out); Ab1 = dE/dA_1 with row stride ld[1]
+cudaError_t tf32_input_grad1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, const float* Ab1,
+                             float* g, DevStatus* status, cudaStream_t s, int* launches)
+{
+    Tf32Bufs t;
+    tf32_carve(p, N, mask, static_cast<char*>(ws), t);
+    const int D = p.ld[0], h1 = p.ld[1];
+    LayerArgs la = tc_layer_args(p, 0);
+    k_dact_split_tf32<<<blocks(N * t.ldz), 256, 0, s>>>(N, h1, t.ldz, la, b.seg_off, Ab1, b.Z[1],
+                                                        parts_of(t.Zb, kPartsFwd));
+    ++*launches;
+    TcMaps m;
+    cudaError_t e = tf32_maps(m, kPartsFwd, t.Zb, N, h1, t.ldz, kTcBM, t.Wb, (int64_t)p.S * t.npb, h1, t.kpb, t.bnb);
+    if (e != cudaSuccess) return e;
+    TcArgs ta = tf32_base(p, b, t, status);
+    for (int q = 0; q < p.S; ++q) ta.N[q] = p.widths[q][0];
+    ta.K = h1; ta.BN = t.bnb; ta.n_pad = t.npb;
+    ta.outF = g; ta.ldF = D;
+    e = launch_tc<TC_BWD_OUT, kPartsFwd, true>(m, ta, N, D, s);
+    ++*launches;
+    return e;
+}
+
+// tangent of the first layer along Gdot: Zd_1 = Gdot W_1^T, Ad_1 = act'(Z_1) Zd_1
+cudaError_t tf32_tangent1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, const float* Gdot,
+                          DevStatus* status, cudaStream_t s, int* launches)
+{
+    Tf32Bufs t;
+    tf32_carve(p, N, mask, static_cast<char*>(ws), t);
+    const int D = p.ld[0];
+    // the forward pass is done with its split of G: the buffers now take Gdot
+    k_split_tf32<<<blocks(N * D), 256, 0, s>>>(N, D, D, D, Gdot, parts_of(t.G, kPartsTan));
+    ++*launches;
+    TcMaps m;
+    cudaError_t e = tf32_maps(m, kPartsTan, t.G, N, D, D, kTcBM, t.Wf, (int64_t)p.S * t.npf, D, t.kpf, t.bnf);
+    if (e != cudaSuccess) return e;
+    TcArgs ta = tf32_base(p, b, t, status);
+    for (int q = 0; q < p.S; ++q) { ta.N[q] = p.widths[q][1]; ta.act[q] = p.acts[q][0]; }
+    ta.K = D; ta.BN = t.bnf; ta.n_pad = t.npf;
+    ta.outF = b.Zd[1]; ta.ldF = p.ld[1];
+    ta.outA = b.Ad[1]; ta.ldA = p.ld[1];
+    ta.Zin = b.Z[1]; ta.ldZ = p.ld[1];
+    e = launch_tc<TC_TAN32, kPartsTan, true>(m, ta, N, p.ld[1], s);
+    ++*launches;
+    return e;
+}
+
+// Weight gradient of layer l+1 (l = 0: the first layer, inputs G and Gdot):
+//   dW = Zb^T A_l + Zdb^T Adot_l,  db = sum of Zb over the species' atoms,
+// sums over atoms on the tensor cores (TF32 pairs), written into dtheta.  Zb, Zdb: the
+// layer's adjoints [N, ld[l+1]]; A, Ad: its inputs [N, ld[l]].
+cudaError_t tf32_wgrad(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, int l, const float* A,
+                       const float* Ad, float* dtheta, DevStatus* status, cudaStream_t s, int* launches)
+{
+    Tf32Bufs t;
+    tf32_carve(p, N, mask, static_cast<char*>(ws), t);
+    const int K = p.ld[l], M = p.ld[l + 1];
+    const int64_t ldT = 2 * t.Kp;
+    Widths wz{}, wg{};
+    for (int q = 0; q < p.S; ++q) { wz.n[q] = p.widths[q][l + 1]; wg.n[q] = p.widths[q][l]; }
+    const unsigned ctiles = (unsigned)(t.Kp / 32);
+    const Parts3 zt = parts_of(t.ZT, kPartsW), gt = parts_of(t.GT, kPartsW);
+    k_transpose_split<<<dim3(ctiles, (unsigned)((M + 31) / 32)), 256, 0, s>>>(
+        b.Zb, M, p.S, b.seg_off, t.pstart, wz, M, -1, zt, ldT, 0);
+    k_transpose_split<<<dim3(ctiles, (unsigned)((M + 31) / 32)), 256, 0, s>>>(
+        b.Zdb, M, p.S, b.seg_off, t.pstart, wz, M, -1, zt, ldT, t.Kp);
+    k_transpose_split<<<dim3(ctiles, (unsigned)((K + 1 + 31) / 32)), 256, 0, s>>>(
+        A, K, p.S, b.seg_off, t.pstart, wg, K + 1, K, gt, ldT, 0);
+    k_transpose_split<<<dim3(ctiles, (unsigned)((K + 1 + 31) / 32)), 256, 0, s>>>(
+        Ad, K, p.S, b.seg_off, t.pstart, wg, K + 1, -1, gt, ldT, t.Kp);
+    *launches += 4;
+    const int bn = tc_bn(K + 1, TcCfg<kPartsW>::kMaxBN);
+    TcMaps m;
+    cudaError_t e = tf32_maps(m, kPartsW, t.ZT, M, ldT, ldT, kTcBM, t.GT, K + 1, ldT, ldT, bn);
+    if (e != cudaSuccess) return e;
+    TcArgs ta = tf32_base(p, b, t, status);
+    ta.BN = bn;
+    ta.item_start = t.items; ta.pstart = t.pstart; ta.Kp = (int)t.Kp; ta.chunk = t.chunk;
+    ta.part = t.part; ta.ldn = K + 1; ta.Mvalid = M; ta.Nvalid = K + 1;
+    dim3 grid((unsigned)t.items_max, (unsigned)((K + 1 + bn - 1) / bn), (unsigned)((M + kTcBM - 1) / kTcBM));
+    e = launch_tc_grid<TC_WGRAD, kPartsW, true>(m, ta, grid, s);
+    if (e != cudaSuccess) return e;
+    LayerArgs la = tc_layer_args(p, l);
+    k_wgrad_reduce<<<blocks((int64_t)p.S * M * (K + 1)), 256, 0, s>>>(la, t.items, M, K + 1, t.part, dtheta);
+    *launches += 2;
     return cudaGetLastError();
 }
 

@@ -68,11 +68,20 @@ def test_descriptors_match_oracle(torch_cuda, name):
     assert err <= H.TOL_G
 
 
+# FP32 networks: the first layer's products on the tensor cores as TF32 parts (bit mask:
+# 1 forward, 2 input gradient, 4 tangent, 8 weight gradient; 12 is the default) or
+# everything on the CUDA cores (0).  The default and the all-CUDA-core path must meet the
+# FP32 tolerances; 2 | 12 (input gradient as well) is checked too.
+FP32_PATHS = [12, 0, 14]
+
+
+@pytest.mark.parametrize("path", FP32_PATHS)
 @pytest.mark.parametrize("name", CASES)
-def test_energy_forces_virial_fp32(torch_cuda, name):
+def test_energy_forces_virial_fp32(torch_cuda, name, path):
     torch = torch_cuda
     wl = _special(name)
     pot = P.Potential(wl.desc, wl.archs)
+    P.panna_set_tuning(pot.ctx, "mlp_fp32", path)
     sysd = P.DeviceSystem(wl.system)
     theta = torch.as_tensor(wl.theta, dtype=torch.float32, device="cuda")
     E, Ea, F, V = pot.energy_forces(sysd, theta, P.PANNA_MLP_FP32)
@@ -84,8 +93,8 @@ def test_energy_forces_virial_fp32(torch_cuda, name):
     eerr = float(np.abs(E.cpu().numpy() - ref["E_cfg"]).max() / scale)
     verr = float(np.abs(V.cpu().numpy() - ref["virial"]).max() / (np.abs(ref["virial"]).max() + 1e-30))
     aerr = float(np.abs(Ea.cpu().numpy() - ref["E_atom"]).max() / (np.abs(ref["E_atom"]).max() + 1e-30))
-    print("%s: max|dF|/rms %.3g (rms %.3g), |dE|/sum|Ei| %.3g, virial %.3g, atom E %.3g" % (
-        name, ferr, rms, eerr, verr, aerr))
+    print("%s path %d: max|dF|/rms %.3g (rms %.3g), |dE|/sum|Ei| %.3g, virial %.3g, atom E %.3g" % (
+        name, path, ferr, rms, eerr, verr, aerr))
     assert eerr <= H.TOL_E
     assert aerr <= 10 * H.TOL_E
     if rms > 0:
@@ -93,8 +102,9 @@ def test_energy_forces_virial_fp32(torch_cuda, name):
     assert verr <= 10 * H.TOL_F_FP32
 
 
-@pytest.mark.parametrize("name", ["molecules16", "ragged8"])
-def test_loss_gradient_fp32(torch_cuda, name):
+@pytest.mark.parametrize("path", FP32_PATHS)
+@pytest.mark.parametrize("name", ["molecules16", "ragged8", "diamond64", "water512"])
+def test_loss_gradient_fp32(torch_cuda, name, path):
     torch = torch_cuda
     wl = W.make(name)
     rng = np.random.default_rng(1)
@@ -102,6 +112,7 @@ def test_loss_gradient_fp32(torch_cuda, name):
         wl.e_ref = rng.normal(size=wl.system.n_cfg) * 10
         wl.f_ref = rng.normal(size=(wl.system.n_atoms, 3))
     pot = P.Potential(wl.desc, wl.archs)
+    P.panna_set_tuning(pot.ctx, "mlp_fp32", path)
     sysd = P.DeviceSystem(wl.system)
     th32 = wl.theta.astype(np.float32)
     theta = torch.as_tensor(th32, device="cuda")
@@ -112,7 +123,7 @@ def test_loss_gradient_fp32(torch_cuda, name):
                   f_ref=wl.f_ref.astype(np.float32).astype(np.float64), w_force=wl.w_force, param_grad=True)
     lerr = abs(float(loss.item()) - ref["loss"]) / abs(ref["loss"])
     errs = H.layer_errors(wl.archs, g.cpu().numpy().astype(np.float64), ref["dtheta"])
-    print("%s loss rel err %.3g, dtheta layer errs %s" % (name, lerr, ["%.2g" % e for e in errs]))
+    print("%s path %d: loss rel err %.3g, dtheta layer errs %s" % (name, path, lerr, ["%.2g" % e for e in errs]))
     assert lerr <= 1e-5
     assert max(errs) <= H.TOL_DTHETA
 
@@ -167,10 +178,16 @@ def test_bad_species_is_reported(torch_cuda):
     assert torch.isfinite(F).all()
 
 
-def test_results_are_deterministic(torch_cuda):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_results_are_deterministic(torch_cuda, variant):
+    # descriptors and energies bit for bit with blocked (0) and flattened (1) descriptor
+    # kernels.  Forces are summed over centres with atomics (F_j -= q_ij from every centre
+    # i), so they and the training gradient that depends on them agree to rounding only.
     torch = torch_cuda
     wl = W.make("water512")
     pot = P.Potential(wl.desc, wl.archs)
+    P.panna_set_tuning(pot.ctx, "descriptor", variant)
+    P.panna_set_tuning(pot.ctx, "jvp", variant)
     sysd = P.DeviceSystem(wl.system)
     theta = torch.as_tensor(wl.theta, dtype=torch.float32, device="cuda")
     G1 = pot.descriptors(sysd)
@@ -179,15 +196,21 @@ def test_results_are_deterministic(torch_cuda):
     E1 = pot.energy_forces(sysd, theta)[0]
     E2 = pot.energy_forces(sysd, theta)[0]
     assert torch.equal(E1, E2)
+    E_ref = torch.zeros(sysd.n_cfg, dtype=torch.float64, device="cuda")
+    F_ref = torch.zeros((sysd.n_atoms, 3), dtype=torch.float32, device="cuda")
+    g1 = pot.loss_grad(sysd, theta, E_ref, F_ref, 0.1)[1]
+    g2 = pot.loss_grad(sysd, theta, E_ref, F_ref, 0.1)[1]
+    assert (g1 - g2).abs().max().item() <= 1e-5 * g1.abs().max().item()
 
 
 @pytest.mark.parametrize("name", ["molecules16", "fcc256", "ragged8", "tiny_cell"])
 @pytest.mark.parametrize("variant", [0, 1])
-def test_adjoint_variants(torch_cuda, name, variant):
+def test_adjoint_and_descriptor_variants(torch_cuda, name, variant):
     torch = torch_cuda
     wl = _special(name)
     pot = P.Potential(wl.desc, wl.archs)
     P.panna_set_tuning(pot.ctx, "adjoint", variant)
+    P.panna_set_tuning(pot.ctx, "descriptor", variant)
     sysd = P.DeviceSystem(wl.system)
     theta = torch.as_tensor(wl.theta, dtype=torch.float32, device="cuda")
     E, Ea, F, V = pot.energy_forces(sysd, theta, P.PANNA_MLP_FP32)
@@ -200,3 +223,27 @@ def test_adjoint_variants(torch_cuda, name, variant):
         assert np.abs(Fn).max() <= 1e-5
     verr = float(np.abs(V.cpu().numpy() - ref["virial"]).max() / (np.abs(ref["virial"]).max() + 1e-30))
     assert verr <= 10 * H.TOL_F_FP32
+    aerr = float(np.abs(Ea.cpu().numpy() - ref["E_atom"]).max() / (np.abs(ref["E_atom"]).max() + 1e-30))
+    assert aerr <= 10 * H.TOL_E
+
+
+@pytest.mark.parametrize("name", ["molecules16", "ragged8", "diamond64", "water512"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_jvp_variants_training_gradient(torch_cuda, name, variant):
+    torch = torch_cuda
+    wl = W.make(name)
+    rng = np.random.default_rng(3)
+    e_ref = rng.normal(size=wl.system.n_cfg) * 10
+    f_ref = rng.normal(size=(wl.system.n_atoms, 3))
+    pot = P.Potential(wl.desc, wl.archs)
+    P.panna_set_tuning(pot.ctx, "jvp", variant)
+    sysd = P.DeviceSystem(wl.system)
+    th32 = wl.theta.astype(np.float32)
+    loss, g, E, F = pot.loss_grad(sysd, torch.as_tensor(th32, device="cuda"),
+                                  torch.as_tensor(e_ref, dtype=torch.float64, device="cuda"),
+                                  torch.as_tensor(f_ref, dtype=torch.float32, device="cuda"), 0.5)
+    ref = O.batch(wl.system, wl.desc, wl.archs, th32.astype(np.float64), e_ref=e_ref,
+                  f_ref=f_ref.astype(np.float32).astype(np.float64), w_force=0.5, param_grad=True)
+    errs = H.layer_errors(wl.archs, g.cpu().numpy().astype(np.float64), ref["dtheta"])
+    print("%s jvp variant %d: dtheta worst layer %.3g" % (name, variant, max(errs)))
+    assert max(errs) <= H.TOL_DTHETA
