@@ -43,7 +43,7 @@ __global__ void k_tiles(int S, const int32_t* __restrict__ seg_off, int32_t* __r
         int t = 0;
         for (int s = 0; s < S; ++s) {
             tile_start[s] = t;
-            t += (seg_off[s + 1] - seg_off[s] + kBM - 1) / kBM;
+            t += (seg_off[s + 1] - seg_off[s] + kGM - 1) / kGM;
         }
         tile_start[S] = t;
     }
@@ -62,93 +62,158 @@ __device__ __forceinline__ bool tile_species(int S, const int32_t* tile_start, i
 //   else     (input gradient):   op(B)[k][n] = W[k*N + n] (W is [K, N])
 // PRO_DACT: A[r][k] is multiplied by act'(Zp[r][k]) on load (layer activation la.pact).
 // EPI_FWD:  C = Z = acc + b, C2 = act(Z);  EPI_TAN: C = acc, C2 = act'(Ze) * acc.
+//
+// 128 x 128 tile per CTA of 256 threads; each thread owns 8 x 8 outputs (rows ty*4 + {0..3}
+// and 64 + ty*4 + {0..3}, likewise columns), so its shared-memory reads are float4 and
+// conflict-free.  K advances 8 at a time through double-buffered shared tiles; the next
+// tile's global loads are issued before the current tile's FMAs.  Every output is one FMA
+// chain in k order, as in a plain dot product.
+struct GemmLoad { float a[4], b[4]; };
+
+template <bool B_TRANS, int PRO>
+__device__ __forceinline__ void gemm_fetch(const LayerArgs& la, int s, const float* __restrict__ A, int lda,
+                                           const float* __restrict__ Zp, int ldp, const float* __restrict__ W,
+                                           int K, int N, int r0, int rend, int n0, int k0, int tid, GemmLoad& g)
+{
+    {   // A tile: 128 rows x 8 k; thread -> row tid/2, k quad (tid&1)*4
+        const int r = r0 + (tid >> 1), kq = k0 + (tid & 1) * 4;
+        const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda & 3) == 0;
+        if (vec && r < rend && kq + 3 < K) {
+            const float4 v = *reinterpret_cast<const float4*>(A + (size_t)r * lda + kq);
+            g.a[0] = v.x; g.a[1] = v.y; g.a[2] = v.z; g.a[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g.a[j] = (r < rend && kq + j < K) ? A[(size_t)r * lda + kq + j] : 0.f;
+        }
+        if (PRO == PRO_DACT && r < rend) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (kq + j < K) g.a[j] *= act_d1(la.pact[s], Zp[(size_t)r * ldp + kq + j]);
+        }
+    }
+    if (B_TRANS) {   // W [N, K]: 128 n x 8 k; thread -> n tid/2, k quad (tid&1)*4
+        const int n = n0 + (tid >> 1), kq = k0 + (tid & 1) * 4;
+        // per-species weights start anywhere in theta: vector loads only from a 16-byte aligned base
+        const bool vec = ((reinterpret_cast<uintptr_t>(W) & 15) == 0) && (K & 3) == 0;
+        if (vec && n < N && kq + 3 < K) {
+            const float4 v = *reinterpret_cast<const float4*>(W + (size_t)n * K + kq);
+            g.b[0] = v.x; g.b[1] = v.y; g.b[2] = v.z; g.b[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g.b[j] = (n < N && kq + j < K) ? W[(size_t)n * K + kq + j] : 0.f;
+        }
+    } else {         // W [K, N]: 8 k x 128 n; thread -> k tid/32, n quad (tid&31)*4
+        const int k = k0 + (tid >> 5), nq = n0 + (tid & 31) * 4;
+        const bool vec = ((reinterpret_cast<uintptr_t>(W) & 15) == 0) && (N & 3) == 0;
+        if (vec && k < K && nq + 3 < N) {
+            const float4 v = *reinterpret_cast<const float4*>(W + (size_t)k * N + nq);
+            g.b[0] = v.x; g.b[1] = v.y; g.b[2] = v.z; g.b[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g.b[j] = (k < K && nq + j < N) ? W[(size_t)k * N + nq + j] : 0.f;
+        }
+    }
+}
+
+template <bool B_TRANS>
+__device__ __forceinline__ void gemm_stash(const GemmLoad& g, float (*As)[kGM], float (*Bs)[kGN], int tid)
+{
+    const int m = tid >> 1, kq = (tid & 1) * 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) As[kq + j][m] = g.a[j];
+    if (B_TRANS) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Bs[kq + j][m] = g.b[j];
+    } else {
+        *reinterpret_cast<float4*>(&Bs[tid >> 5][(tid & 31) * 4]) = make_float4(g.b[0], g.b[1], g.b[2], g.b[3]);
+    }
+}
+
 template <bool B_TRANS, int PRO, int EPI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_gemm(LayerArgs la, const float* __restrict__ theta, const int32_t* __restrict__ seg_off,
        const int32_t* __restrict__ tile_start, const float* __restrict__ A, int lda,
        const float* __restrict__ Zp, int ldp, float* __restrict__ C, int ldc, float* __restrict__ C2,
        const float* __restrict__ Ze, int lde)
 {
-    __shared__ float As[kBK][kBM + 4];
-    __shared__ float Bs[kBK][kBN + 4];
+    __shared__ __align__(16) float As[2][kGK][kGM];
+    __shared__ __align__(16) float Bs[2][kGK][kGN];
     int s;
     if (!tile_species(la.S, tile_start, blockIdx.x, s)) return;
     const int K = la.K[s], N = la.N[s];
-    const int n0 = blockIdx.y * kBN;
+    const int n0 = blockIdx.y * kGN;
     if (n0 >= N) return;
-    const int r0 = seg_off[s] + (blockIdx.x - tile_start[s]) * kBM;
+    const int r0 = seg_off[s] + (blockIdx.x - tile_start[s]) * kGM;
     const int rend = seg_off[s + 1];
     const float* W = theta + la.w_off[s];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    float acc[4][4];
+    float acc[8][8];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += kBK) {
-        {   // A tile: 64 rows x 16 k
-            const int m = tid >> 2, kq = (tid & 3) * 4;
-            const int r = r0 + m;
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    GemmLoad g;
+    gemm_fetch<B_TRANS, PRO>(la, s, A, lda, Zp, ldp, W, K, N, r0, rend, n0, 0, tid, g);
+    gemm_stash<B_TRANS>(g, As[0], Bs[0], tid);
+    __syncthreads();
+    const int nk = (K + kGK - 1) / kGK;
+    for (int t = 0; t < nk; ++t) {
+        const int cur = t & 1;
+        if (t + 1 < nk) gemm_fetch<B_TRANS, PRO>(la, s, A, lda, Zp, ldp, W, K, N, r0, rend, n0, (t + 1) * kGK, tid, g);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int k = k0 + kq + j;
-                float v = 0.f;
-                if (r < rend && k < K) {
-                    v = A[(size_t)r * lda + k];
-                    if (PRO == PRO_DACT) v *= act_d1(la.pact[s], Zp[(size_t)r * ldp + k]);
-                }
-                As[kq + j][m] = v;
-            }
+        for (int kk = 0; kk < kGK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
         }
-        if (B_TRANS) {   // W [N, K]: 64 n x 16 k
-            const int nn = tid >> 2, kq = (tid & 3) * 4;
-            const int n = n0 + nn;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int k = k0 + kq + j;
-                Bs[kq + j][nn] = (n < N && k < K) ? W[(size_t)n * K + k] : 0.f;
-            }
-        } else {         // W [K, N]: 16 k x 64 n
-            const int kk = tid >> 4, nq = (tid & 15) * 4;
-            const int k = k0 + kk;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n = n0 + nq + j;
-                Bs[kk][nq + j] = (n < N && k < K) ? W[(size_t)k * N + n] : 0.f;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kBK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { a[q] = As[kk][ty * 4 + q]; b[q] = Bs[kk][tx * 4 + q]; }
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
-        }
+        if (t + 1 < nk) gemm_stash<B_TRANS>(g, As[cur ^ 1], Bs[cur ^ 1], tid);
         __syncthreads();
     }
+    // epilogue: each thread's 4 consecutive columns go out as one float4 where the row start
+    // is 16-byte aligned, so a warp writes whole 256-byte row segments
     const float* bias = theta + la.b_off[s];
+    const bool vst = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc & 3) == 0 &&
+                     (EPI == EPI_STORE || ((reinterpret_cast<uintptr_t>(C2) & 15) == 0));
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int r = r0 + ty * 4 + p;
+    for (int p = 0; p < 8; ++p) {
+        const int r = r0 + (p < 4 ? ty * 4 + p : 64 + ty * 4 + p - 4);
         if (r >= rend) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int n = n0 + tx * 4 + q;
-            if (n >= N) continue;
-            float v = acc[p][q];
-            if (EPI == EPI_FWD) {
-                v += bias[n];
-                C[(size_t)r * ldc + n] = v;
-                C2[(size_t)r * ldc + n] = act_f(la.act[s], v);
-            } else if (EPI == EPI_TAN) {
-                C[(size_t)r * ldc + n] = v;
-                C2[(size_t)r * ldc + n] = act_d1(la.act[s], Ze[(size_t)r * lde + n]) * v;
+        for (int h = 0; h < 2; ++h) {
+            const int nb = n0 + h * 64 + tx * 4;
+            float v[4], v2[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = nb + j;
+                v[j] = acc[p][h * 4 + j];
+                v2[j] = 0.f;
+                if (n >= N) continue;
+                if (EPI == EPI_FWD) {
+                    v[j] += bias[n];
+                    v2[j] = act_f(la.act[s], v[j]);
+                } else if (EPI == EPI_TAN) {
+                    v2[j] = act_d1(la.act[s], Ze[(size_t)r * lde + n]) * v[j];
+                }
+            }
+            float* c = C + (size_t)r * ldc + nb;
+            float* c2 = EPI == EPI_STORE ? nullptr : C2 + (size_t)r * ldc + nb;
+            if (vst && nb + 3 < N) {
+                *reinterpret_cast<float4*>(c) = make_float4(v[0], v[1], v[2], v[3]);
+                if (EPI != EPI_STORE) *reinterpret_cast<float4*>(c2) = make_float4(v2[0], v2[1], v2[2], v2[3]);
             } else {
-                C[(size_t)r * ldc + n] = v;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (nb + j >= N) break;
+                    c[j] = v[j];
+                    if (EPI != EPI_STORE) c2[j] = v2[j];
+                }
             }
         }
     }
@@ -289,7 +354,7 @@ static LayerArgs layer_args(const MlpPlan& p, int l, bool backward)
 
 static dim3 gemm_grid(const MlpPlan& p, int64_t N, int n_max)
 {
-    return dim3((unsigned)((N + kBM - 1) / kBM + p.S), (unsigned)((n_max + kBN - 1) / kBN), 1);
+    return dim3((unsigned)((N + kGM - 1) / kGM + p.S), (unsigned)((n_max + kGN - 1) / kGN), 1);
 }
 
 cudaError_t mlp_tiles(const MlpPlan& p, const int32_t* seg_off, int32_t* tile_start, cudaStream_t s, int* launches)

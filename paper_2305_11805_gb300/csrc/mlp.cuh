@@ -5,7 +5,8 @@
 
 namespace panna {
 
-constexpr int kBM = 64, kBN = 64, kBK = 16;
+constexpr int kBM = 64, kBN = 64, kBK = 16;      // weight-gradient tiles (k_wgrad)
+constexpr int kGM = 128, kGN = 128, kGK = 8;     // layer GEMM tiles (k_gemm): 256 threads, 8 x 8 outputs each
 enum { PRO_NONE = 0, PRO_DACT = 1 };
 enum { EPI_STORE = 0, EPI_FWD = 1, EPI_TAN = 2 };
 

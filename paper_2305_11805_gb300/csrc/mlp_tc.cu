@@ -538,9 +538,77 @@ k_transpose_split(const float* __restrict__ src, int lds, int S, const int32_t* 
     }
 }
 
-// dtheta of one layer from the per-item partial sums, in item order (deterministic):
+// Weight gradient of a narrow layer (M x (K+1) <= 8192 outputs) straight from the row-major
+// adjoints Zb, Zdb [rows, M] and inputs A, Ad [rows, K]: one CTA per (item = species chunk of
+// atoms, split of that chunk); every thread owns up to 32 outputs o = m (K+1) + n (n == K: the
+// bias), rows pass through shared memory 32 at a time.  The partial of (item, split) goes to
+// part[(item * splits + split) * M (K+1) + o], so item order stays the reduction order.
+constexpr int kSmallRows = 32, kSmallOut = 32;
+__global__ void __launch_bounds__(256)
+k_wgrad_small(int S, const int32_t* __restrict__ seg_off, const int32_t* __restrict__ item_start, int chunk,
+              int splits, int M, int K, const float* __restrict__ Zb, const float* __restrict__ Zdb,
+              const float* __restrict__ A, const float* __restrict__ Ad, float* __restrict__ part)
+{
+    extern __shared__ float sh[];
+    const int item = blockIdx.x;
+    if (item >= item_start[S]) return;
+    int s = 0;
+    while (item >= item_start[s + 1]) ++s;
+    const int per = (chunk / splits + kSmallRows - 1) / kSmallRows * kSmallRows;
+    const int c0 = (item - item_start[s]) * chunk + blockIdx.y * per;
+    const int cend = min((item - item_start[s] + 1) * chunk, c0 + per);
+    const int cnt = seg_off[s + 1] - seg_off[s];
+    const int a0 = seg_off[s] + min(cnt, c0), a1 = seg_off[s] + min(cnt, cend);
+    float* sZ = sh;
+    float* sZd = sZ + kSmallRows * M;
+    float* sA = sZd + kSmallRows * M;
+    float* sAd = sA + kSmallRows * K;
+    const int O = M * (K + 1);
+    const int tid = threadIdx.x;
+    float acc[kSmallOut];
+#pragma unroll
+    for (int j = 0; j < kSmallOut; ++j) acc[j] = 0.f;
+    for (int r0 = a0; r0 < a1; r0 += kSmallRows) {
+        const int nr = min(kSmallRows, a1 - r0);
+        __syncthreads();
+        for (int idx = tid; idx < kSmallRows * M; idx += 256) {
+            const int rr = idx / M;
+            sZ[idx] = rr < nr ? Zb[(size_t)r0 * M + idx] : 0.f;
+            sZd[idx] = rr < nr ? Zdb[(size_t)r0 * M + idx] : 0.f;
+        }
+        for (int idx = tid; idx < kSmallRows * K; idx += 256) {
+            const int rr = idx / K;
+            sA[idx] = rr < nr ? A[(size_t)r0 * K + idx] : 0.f;
+            sAd[idx] = rr < nr ? Ad[(size_t)r0 * K + idx] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSmallOut; ++j) {
+            const int o = j * 256 + tid;
+            if (o >= O) break;
+            const int m = o / (K + 1), n = o % (K + 1);
+            float a = acc[j];
+            if (n < K) {
+                for (int rr = 0; rr < kSmallRows; ++rr)
+                    a = fmaf(sZ[rr * M + m], sA[rr * K + n], fmaf(sZd[rr * M + m], sAd[rr * K + n], a));
+            } else {
+                for (int rr = 0; rr < kSmallRows; ++rr) a += sZ[rr * M + m];
+            }
+            acc[j] = a;
+        }
+    }
+    float* out = part + ((size_t)item * splits + blockIdx.y) * O;
+#pragma unroll
+    for (int j = 0; j < kSmallOut; ++j) {
+        const int o = j * 256 + tid;
+        if (o >= O) break;
+        out[o] = acc[j];
+    }
+}
+
+// dtheta of one layer from the per-item partial sums (splits per item), in order (deterministic):
 // n < K_s: weight W[m][n]; n == ldn - 1 (the row of ones): bias b[m].
-__global__ void k_wgrad_reduce(LayerArgs la, const int32_t* __restrict__ item_start, int Mvalid, int ldn,
+__global__ void k_wgrad_reduce(LayerArgs la, const int32_t* __restrict__ item_start, int splits, int Mvalid, int ldn,
                                const float* __restrict__ part, float* __restrict__ dtheta)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -551,7 +619,8 @@ __global__ void k_wgrad_reduce(LayerArgs la, const int32_t* __restrict__ item_st
     const int K = la.K[s];
     if (m >= la.N[s] || (n >= K && n != ldn - 1)) return;
     float acc = 0.f;
-    for (int it = item_start[s]; it < item_start[s + 1]; ++it) acc += part[((size_t)it * Mvalid + m) * ldn + n];
+    for (int it = item_start[s] * splits; it < item_start[s + 1] * splits; ++it)
+        acc += part[((size_t)it * Mvalid + m) * ldn + n];
     if (n < K) dtheta[la.w_off[s] + (int64_t)m * K + n] = acc;
     else dtheta[la.b_off[s] + m] = acc;
 }
@@ -1076,6 +1145,21 @@ cudaError_t tf32_wgrad(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* w
     Tf32Bufs t;
     tf32_carve(p, N, mask, static_cast<char*>(ws), t);
     const int K = p.ld[l], M = p.ld[l + 1];
+    LayerArgs la = tc_layer_args(p, l);
+    const int O = M * (K + 1);
+    if (l > 0 && O <= 256 * kSmallOut && M + K <= 192) {
+        // narrow layer: CUDA cores, no transposed copies (row staging <= 48 KB of shared memory)
+        size_t part_max = 0;
+        for (int q = 0; q < p.L; ++q) part_max = std::max(part_max, (size_t)p.ld[q + 1] * (p.ld[q] + 1));
+        const int splits = (int)std::max<size_t>(1, std::min<size_t>(8, part_max / O));
+        const size_t smem = (size_t)kSmallRows * 2 * (M + K) * sizeof(float);
+        dim3 grid((unsigned)t.items_max, (unsigned)splits);
+        k_wgrad_small<<<grid, 256, smem, s>>>(p.S, b.seg_off, t.items, t.chunk, splits, M, K, b.Zb, b.Zdb, A, Ad,
+                                             t.part);
+        k_wgrad_reduce<<<blocks((int64_t)p.S * O), 256, 0, s>>>(la, t.items, splits, M, K + 1, t.part, dtheta);
+        *launches += 2;
+        return cudaGetLastError();
+    }
     const int64_t ldT = 2 * t.Kp;
     Widths wz{}, wg{};
     for (int q = 0; q < p.S; ++q) { wz.n[q] = p.widths[q][l + 1]; wg.n[q] = p.widths[q][l]; }
@@ -1101,8 +1185,7 @@ cudaError_t tf32_wgrad(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* w
     dim3 grid((unsigned)t.items_max, (unsigned)((K + 1 + bn - 1) / bn), (unsigned)((M + kTcBM - 1) / kTcBM));
     e = launch_tc_grid<TC_WGRAD, kPartsW, true>(m, ta, grid, s);
     if (e != cudaSuccess) return e;
-    LayerArgs la = tc_layer_args(p, l);
-    k_wgrad_reduce<<<blocks((int64_t)p.S * M * (K + 1)), 256, 0, s>>>(la, t.items, M, K + 1, t.part, dtheta);
+    k_wgrad_reduce<<<blocks((int64_t)p.S * M * (K + 1)), 256, 0, s>>>(la, t.items, 1, M, K + 1, t.part, dtheta);
     *launches += 2;
     return cudaGetLastError();
 }
