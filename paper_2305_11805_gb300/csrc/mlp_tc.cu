@@ -14,10 +14,10 @@
 // Rows are atoms in species order; a CTA owns one 128-row tile of one species (tile
 // table on the device) and one N tile of up to 256 columns.
 //
-// CTA of 6 warps: warp 0 issues TMA loads into a 4-stage ring (mbarrier full/empty),
+// CTA of 10 warps: warp 0 issues TMA loads into a 2-4 stage ring (mbarrier full/empty),
 // warp 1 owns the TMEM allocation and one lane issues tcgen05.mma (M = 128, N = BN,
-// K = 16 BF16 or 8 TF32 per instruction, 4 per 128-byte K chunk) and tcgen05.commit; warps 2..5 read the
-// accumulator with tcgen05.ld (each warp its 32-lane quarter) and run the epilogue.
+// K = 16 BF16 or 8 TF32 per instruction, 4 per 128-byte K chunk) and tcgen05.commit; warps 2..9
+// read the accumulator with tcgen05.ld (two warps per 32-lane quarter) and run the epilogue.
 // Every wait is bounded: on time-out the CTA sets PANNA_ERR_TIMEOUT, drains what it
 // issued, frees its TMEM and returns.
 #include <cuda.h>
@@ -34,7 +34,8 @@ namespace panna {
 namespace {
 
 constexpr int kTcBM = 128, kTcBK = 64;   // kTcBK: BF16 elements per 128-byte K chunk (32 for TF32)
-constexpr int kTcThreads = 192;
+constexpr int kTcEpiWarps = 8;                          // two per TMEM lane quarter
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kSpinLimit = 1ll << 25;
 constexpr uint32_t kTileA = kTcBM * kTcBK * 2;           // 16 KiB: one 128 x 64 BF16 tile
@@ -374,44 +375,82 @@ k_tc_gemm(const __grid_constant__ TcMaps tm, TcArgs a)
             if (!ok) mbar_wait(accf, 0, nullptr);   // no TMEM release under running MMAs
         }
     } else {
-        const int q = warp & 3;                    // TMEM lane quarter of this warp
-        const int r = row0 + q * 32 + lane;        // this thread's row (WGRAD: output m)
-        const int m = m0 + q * 32 + lane;
-        if (mbar_wait(accf, 0, abort_flag)) {
+        // Epilogue in two passes through shared memory (the pipeline buffers are free once
+        // every MMA has completed).  Pass 1: the two warps of each TMEM lane quarter copy their
+        // 32 rows into a [128][BN + 4] FP32 tile (16-byte aligned rows), alternating 16-column
+        // chunks.  Pass 2: warp w sweeps rows w, w + 8, ...; each lane takes 4 consecutive
+        // columns, so loads and stores of a row are contiguous (float4 where aligned).  Every
+        // epilogue warp reaches the named barrier, also after a failed wait.
+        const int ew = warp - 2;                   // epilogue warp 0..7
+        const int q = warp & 3;                    // TMEM lane quarter (hardware: warp id mod 4)
+        const int half = ew >> 2;
+        const int ldt = a.BN + 4;
+        float* tile_s = reinterpret_cast<float*>(smem);
+        const bool ok = mbar_wait(accf, 0, abort_flag);
+        if (ok) {
             tc_fence_after();
-            const int Ns = EPI == TC_WGRAD ? a.Nvalid : a.N[s];
-            for (int c0 = 0; c0 < a.BN; c0 += 16) {
+            for (int c0 = half * 16; c0 < a.BN; c0 += 32) {
                 float v[16];
                 tc_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                if (EPI == TC_WGRAD ? m >= a.Mvalid : r >= rend) continue;
-                const int nb = n0 + c0;
+                float4* dst = reinterpret_cast<float4*>(tile_s + (q * 32 + lane) * ldt + c0);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int n = nb + j;
-                    if (n >= Ns) break;
-                    if (EPI == TC_FWD) {
-                        const float z = v[j] + a.bias[s * a.n_pad + n];
-                        a.outF[(size_t)r * a.ldF + n] = z;
-                        store_split(a.outH, PARTS >= 2 ? a.outL : nullptr, (size_t)r * a.ldH + n, act_f(a.act[s], z));
-                    } else if (EPI == TC_BWD_MID) {
-                        const float zb = v[j] * act_d1(a.act[s], a.Zin[(size_t)r * a.ldZ + n]);
-                        store_split(a.outH, PARTS >= 2 ? a.outL : nullptr, (size_t)r * a.ldH + n, zb);
-                    } else if (EPI == TC_FWD32) {
-                        const float z = v[j] + a.bias[s * a.n_pad + n];
-                        a.outF[(size_t)r * a.ldF + n] = z;
-                        a.outA[(size_t)r * a.ldA + n] = act_f(a.act[s], z);
-                    } else if (EPI == TC_TAN32) {
-                        a.outF[(size_t)r * a.ldF + n] = v[j];
-                        a.outA[(size_t)r * a.ldA + n] = act_d1(a.act[s], a.Zin[(size_t)r * a.ldZ + n]) * v[j];
-                    } else if (EPI == TC_WGRAD) {
-                        a.part[((size_t)item * a.Mvalid + m) * a.ldn + n] = v[j];
-                    } else {
-                        a.outF[(size_t)r * a.ldF + n] = v[j];
-                    }
-                }
+                for (int j2 = 0; j2 < 4; ++j2) dst[j2] = make_float4(v[4 * j2], v[4 * j2 + 1], v[4 * j2 + 2], v[4 * j2 + 3]);
             }
         } else {
             *abort_flag = 1;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kTcEpiWarps) : "memory");
+        if (!*abort_flag) {
+            const int Ns = EPI == TC_WGRAD ? a.Nvalid : a.N[s];
+            for (int row = ew; row < kTcBM; row += kTcEpiWarps) {
+                const int r = row0 + row, m = m0 + row;
+                if (EPI == TC_WGRAD ? m >= a.Mvalid : r >= rend) continue;
+                for (int col = lane * 4; col < a.BN; col += 128) {
+                    const int n = n0 + col;
+                    if (n >= Ns) break;
+                    const float4 t4 = *reinterpret_cast<const float4*>(tile_s + row * ldt + col);
+                    const float v[4] = {t4.x, t4.y, t4.z, t4.w};
+                    const int nv = min(4, Ns - n);
+                    if (EPI == TC_WGRAD) {
+                        float* o = a.part + ((size_t)item * a.Mvalid + m) * a.ldn + n;
+                        for (int j2 = 0; j2 < nv; ++j2) o[j2] = v[j2];
+                        continue;
+                    }
+                    float o1[4], o2[4];
+#pragma unroll
+                    for (int j2 = 0; j2 < 4; ++j2) {
+                        o1[j2] = v[j2];
+                        o2[j2] = 0.f;
+                        if (j2 >= nv) continue;
+                        if (EPI == TC_FWD || EPI == TC_FWD32) {
+                            o1[j2] = v[j2] + a.bias[s * a.n_pad + n + j2];
+                            o2[j2] = act_f(a.act[s], o1[j2]);
+                        } else if (EPI == TC_BWD_MID) {
+                            o2[j2] = v[j2] * act_d1(a.act[s], a.Zin[(size_t)r * a.ldZ + n + j2]);
+                        } else if (EPI == TC_TAN32) {
+                            o2[j2] = act_d1(a.act[s], a.Zin[(size_t)r * a.ldZ + n + j2]) * v[j2];
+                        }
+                    }
+                    if (EPI == TC_FWD || EPI == TC_FWD32 || EPI == TC_TAN32 || EPI == TC_BWD_OUT) {
+                        float* o = a.outF + (size_t)r * a.ldF + n;
+                        if (nv == 4 && ((reinterpret_cast<uintptr_t>(o) & 15) == 0))
+                            *reinterpret_cast<float4*>(o) = make_float4(o1[0], o1[1], o1[2], o1[3]);
+                        else
+                            for (int j2 = 0; j2 < nv; ++j2) o[j2] = o1[j2];
+                    }
+                    if (EPI == TC_FWD32 || EPI == TC_TAN32) {
+                        float* o = a.outA + (size_t)r * a.ldA + n;
+                        if (nv == 4 && ((reinterpret_cast<uintptr_t>(o) & 15) == 0))
+                            *reinterpret_cast<float4*>(o) = make_float4(o2[0], o2[1], o2[2], o2[3]);
+                        else
+                            for (int j2 = 0; j2 < nv; ++j2) o[j2] = o2[j2];
+                    }
+                    if (EPI == TC_FWD || EPI == TC_BWD_MID) {
+                        for (int j2 = 0; j2 < nv; ++j2)
+                            store_split(a.outH, PARTS >= 2 ? a.outL : nullptr, (size_t)r * a.ldH + n + j2, o2[j2]);
+                    }
+                }
+            }
         }
     }
     tc_fence_before();
