@@ -24,6 +24,7 @@ _dp = C.POINTER(C.c_double)
 _i64p = C.POINTER(C.c_int64)
 _i32p = C.POINTER(C.c_int32)
 _u8p = C.POINTER(C.c_uint8)
+_u32p = C.POINTER(C.c_uint32)
 
 
 class OrcDesc(C.Structure):
@@ -73,6 +74,14 @@ def lib():
         L.orc_sampled.argtypes = [C.c_int64, _dp, _i32p, _dp, _u8p, C.POINTER(OrcDesc),
                                   C.POINTER(OrcArch), _dp, _i64p, C.c_int64, _i64p, C.c_int64,
                                   _i32p, _i32p, _i64p, _dp, _dp, _dp]
+        L.orc_philox4x32_10.restype = None
+        L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_gauss3.restype = None
+        L.orc_gauss3.argtypes = [C.c_uint64, C.c_int64, C.c_int64, _dp]
+        L.orc_md_baoab.restype = C.c_int
+        L.orc_md_baoab.argtypes = [C.c_int64, _i64p, _dp, _dp, _i32p, _dp, _u8p, C.POINTER(OrcDesc),
+                                   C.POINTER(OrcArch), _dp, _i64p, _dp, C.c_double, C.c_double,
+                                   C.c_double, C.c_uint64, C.c_int64, C.c_int64, _dp, _dp]
         _lib = L
     return _lib
 
@@ -220,6 +229,45 @@ def workload_batch(wl, want_G=False, train=False):
     return batch(wl.system, wl.desc, wl.archs, wl.theta, want_G=want_G,
                  e_ref=wl.e_ref if train else None, f_ref=wl.f_ref if train else None,
                  w_force=wl.w_force, param_grad=train)
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of a counter of four 32-bit words and a key of two (see orc_philox4x32_10)."""
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_ptr(c, _u32p), _ptr(k, _u32p), _ptr(out, _u32p))
+    return out
+
+
+def gauss3(seed: int, atom: int, step: int):
+    g = np.zeros(3)
+    lib().orc_gauss3(int(seed), int(atom), int(step), _ptr(g, _dp))
+    return g
+
+
+def md_baoab(system, desc, archs, theta, vel, mass, dt, temperature, friction, seed, step0, n_steps):
+    """BAOAB Langevin trajectory in FP64 (forces recomputed from scratch every step).
+    Returns dict(pos, vel, F, E_traj [n_steps, n_cfg])."""
+    s = system
+    h = _DescHolder(desc)
+    off = np.ascontiguousarray(s.atom_off, np.int64)
+    pos = np.array(s.pos, np.float64, copy=True)
+    v = np.array(vel, np.float64, copy=True).reshape(-1, 3)
+    spec = np.ascontiguousarray(s.species, np.int32)
+    cell = np.ascontiguousarray(s.cell, np.float64)
+    pbc = np.ascontiguousarray(s.pbc, np.uint8)
+    arr = _archs(archs)
+    th = np.ascontiguousarray(theta, np.float64)
+    toff = _theta_off(archs)
+    m = np.ascontiguousarray(mass, np.float64)
+    F = np.zeros((s.n_atoms, 3))
+    E = np.zeros((max(int(n_steps), 1), s.n_cfg))
+    lib().orc_md_baoab(s.n_cfg, _ptr(off, _i64p), _ptr(pos, _dp), _ptr(v, _dp), _ptr(spec, _i32p),
+                       _ptr(cell, _dp), _ptr(pbc, _u8p), C.byref(h.s), arr, _ptr(th, _dp), _ptr(toff, _i64p),
+                       _ptr(m, _dp), float(dt), float(temperature), float(friction), int(seed), int(step0),
+                       int(n_steps), _ptr(F, _dp), _ptr(E, _dp))
+    return dict(pos=pos, vel=v, F=F, E_traj=E[:int(n_steps)])
 
 
 def sampled(system, cfg: int, desc, archs, theta, samples: Sequence[int], cap: int = 512):

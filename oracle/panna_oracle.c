@@ -697,3 +697,99 @@ int orc_sampled(int64_t n, const double* pos, const int32_t* species, const doub
     work_free(&wk);
     return 0;
 }
+
+/* ------------------------------------------------------------------ Langevin dynamics
+ *
+ * Units: positions A, velocities A/fs, time fs, masses amu, energies eV, temperature K.
+ * Acceleration of a force of 1 eV/A on 1 amu: e / (amu 1e-10 m) = 9.648533212e17 m/s^2
+ * = 9.648533212e-3 A/fs^2.  Boltzmann constant 8.617333262e-5 eV/K (exact SI values).
+ */
+#define ORC_ACC 9.648533212e-3
+#define ORC_KB 8.617333262e-5
+
+/* Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1,
+ * 2, 3", SC'11): ten rounds on a counter of four 32-bit words with a key of two; each round
+ * multiplies words 0 and 2 by two constants (64-bit products split in high and low halves),
+ * mixes the high halves with the other words and the key, and the key advances by two Weyl
+ * constants between rounds. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        const uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Three standard normal numbers for atom a at step t: the four words of Philox with
+ * counter (a low, a high, t low, t high) and key (seed low, seed high), as uniforms
+ * u = (x + 1/2) 2^-32 in (0, 1), through Box-Muller: sqrt(-2 ln u0) (cos, sin)(2 pi u1),
+ * sqrt(-2 ln u2) cos(2 pi u3). */
+void orc_gauss3(uint64_t seed, int64_t a, int64_t t, double g[3])
+{
+    const uint32_t ctr[4] = {(uint32_t)a, (uint32_t)((uint64_t)a >> 32), (uint32_t)t, (uint32_t)((uint64_t)t >> 32)};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    double u[4];
+    for (int k = 0; k < 4; ++k) u[k] = ((double)x[k] + 0.5) * (1.0 / 4294967296.0);
+    const double two_pi = 6.283185307179586476925286766559;
+    const double r01 = sqrt(-2.0 * log(u[0])), r23 = sqrt(-2.0 * log(u[2]));
+    g[0] = r01 * cos(two_pi * u[1]);
+    g[1] = r01 * sin(two_pi * u[1]);
+    g[2] = r23 * cos(two_pi * u[3]);
+}
+
+/* BAOAB Langevin dynamics (Leimkuhler and Matthews, 2013) on every configuration of a
+ * batch, forces from orc_batch at every step (no neighbour-list reuse):
+ *   B: v += dt/2 F/m;  A: x += dt/2 v;  O: v = c1 v + c2 sqrt(kB T / m) g;  A: x += dt/2 v;
+ *   F = F(x);  B: v += dt/2 F/m;     c1 = exp(-friction dt), c2 = sqrt(1 - c1^2),
+ * g the three normals of orc_gauss3(seed, atom, step0 + step).  With temperature 0 and
+ * friction 0 this is velocity Verlet.  pos, vel [N*3] in/out; F [N*3] out (forces at the
+ * final positions); E_traj [n_steps * n_cfg] (may be NULL): energies after each step. */
+int orc_md_baoab(int64_t n_cfg, const int64_t* atom_off, double* pos, double* vel, const int32_t* species,
+                 const double* cell, const uint8_t* pbc, const orc_desc* p, const orc_arch* archs,
+                 const double* theta, const int64_t* theta_off, const double* mass, double dt,
+                 double temperature, double friction, uint64_t seed, int64_t step0, int64_t n_steps,
+                 double* F, double* E_traj)
+{
+    const int64_t N = atom_off[n_cfg];
+    double* E_atom = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double* E_cfg = (double*)malloc(sizeof(double) * (size_t)n_cfg);
+    orc_batch(n_cfg, atom_off, pos, species, cell, pbc, p, archs, theta, theta_off, NULL, E_atom, E_cfg, F, NULL,
+              NULL, NULL, 0.0, NULL, NULL, NULL, 0.0, 0.0);
+    const double c1 = exp(-friction * dt), c2 = sqrt(1.0 - c1 * c1);
+    const int thermostat = friction > 0.0 || temperature > 0.0;
+    for (int64_t t = 0; t < n_steps; ++t) {
+        for (int64_t i = 0; i < N; ++i) {
+            const double a = ORC_ACC / mass[species[i]];
+            double g[3] = {0.0, 0.0, 0.0};
+            if (thermostat) orc_gauss3(seed, i, step0 + t, g);
+            const double sig = sqrt(ORC_KB * temperature * a);
+            for (int d = 0; d < 3; ++d) {
+                double v = vel[3 * i + d] + 0.5 * dt * F[3 * i + d] * a;
+                double x = pos[3 * i + d] + 0.5 * dt * v;
+                if (thermostat) v = c1 * v + c2 * sig * g[d];
+                x += 0.5 * dt * v;
+                vel[3 * i + d] = v;
+                pos[3 * i + d] = x;
+            }
+        }
+        orc_batch(n_cfg, atom_off, pos, species, cell, pbc, p, archs, theta, theta_off, NULL, E_atom, E_cfg, F,
+                  NULL, NULL, NULL, 0.0, NULL, NULL, NULL, 0.0, 0.0);
+        for (int64_t i = 0; i < N; ++i) {
+            const double a = ORC_ACC / mass[species[i]];
+            for (int d = 0; d < 3; ++d) vel[3 * i + d] += 0.5 * dt * F[3 * i + d] * a;
+        }
+        if (E_traj) memcpy(E_traj + t * n_cfg, E_cfg, sizeof(double) * (size_t)n_cfg);
+    }
+    free(E_atom);
+    free(E_cfg);
+    return 0;
+}

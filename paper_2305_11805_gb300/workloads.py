@@ -430,12 +430,53 @@ def ragged(seed: int = 0, n_cfg: int = 4096, n_min: int = 32, n_max: int = 4096)
 
 
 # First-layer gains (radial, angular) per workload; see init_weights.
+def _small_cell_margin_ok(pos, L, rc) -> bool:
+    """Brute force over every image in an orthorhombic box: no pair distance within
+    CUTOFF_MARGIN of rc (small boxes only)."""
+    L = np.asarray(L, np.float64)
+    m = np.ceil(rc / L).astype(int) + 1
+    shifts = np.stack(np.meshgrid(*[np.arange(-k, k + 1) for k in m], indexing="ij"), -1).reshape(-1, 3) * L
+    d = pos[None, :, None, :] + shifts[None, None, :, :] - pos[:, None, None, :]
+    r = np.sqrt((d ** 2).sum(-1))
+    return not np.any(np.abs(r - rc) < CUTOFF_MARGIN)
+
+
+def carbon16(seed: int = 0, replicas: int = 1) -> Workload:
+    """Diamond carbon, 2 x 1 x 1 conventional cells (16 atoms, a = 3.567 A, sigma = 0.05 A),
+    rc = 5.0 A; descriptor 24 radial shells + 8 R x 16 theta angular bins (D = 152) and the
+    small network 64 - 32 of the paper's carbon tests (Sec. III.B).  `replicas` independent
+    copies (each its own displacements) form a batch for batched dynamics."""
+    rng = np.random.default_rng(seed)
+    a, rc = 3.567, 5.0
+    L = np.array([2 * a, a, a])
+    ideal = np.concatenate([(DIAMOND_BASIS + np.array([cx, 0, 0])) * a for cx in range(2)])
+    pos_all = []
+    for _ in range(replicas):
+        for _ in range(10000):
+            pos = np.mod(ideal + rng.normal(0.0, 0.05, size=ideal.shape), L)
+            if _small_cell_margin_ok(pos, L, rc):
+                break
+        else:
+            raise RuntimeError("could not displace the carbon cell")
+        pos_all.append(pos)
+    n = len(ideal)
+    off = np.arange(replicas + 1, dtype=np.int64) * n
+    sysm = System(off, np.concatenate(pos_all), np.zeros(n * replicas, np.int32),
+                  np.tile(np.diag(L).reshape(1, 9), (replicas, 1)), np.ones((replicas, 3), np.uint8), 1)
+    desc = descriptor_params(1, rc, 24, 16, 8)
+    archs = [_mlp(desc.D, (64, 32))]
+    theta = init_weights(rng, desc, archs, *GAINS["carbon16"])
+    return Workload("carbon16" if replicas == 1 else "carbon16x%d" % replicas, sysm, desc, archs, theta,
+                    mlp_bf16=False, seed=seed)
+
+
 GAINS = {
     "diamond64": (3.5, 4.5),
     "molecules1024": (4.0, 2.0),
     "water32k": (1.5, 0.3),
     "fcc1m": (0.9, 0.9),
     "ragged4096": (3.5, 2.2),
+    "carbon16": (0.7, 0.1),
 }
 
 
@@ -453,5 +494,8 @@ def make(name: str, seed: int = 0) -> Workload:
         "fcc32k": lambda: fcc(seed, 20),
         "ragged4096": lambda: ragged(seed, 4096),
         "ragged8": lambda: ragged(seed, 8, 32, 160),
+        "carbon16": lambda: carbon16(seed),
+        "carbon16x64": lambda: carbon16(seed, 64),
+        "carbon16x4096": lambda: carbon16(seed, 4096),
     }
     return table[name]()
