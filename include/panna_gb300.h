@@ -213,6 +213,49 @@ panna_status panna_set_angular_precision(panna_ctx* ctx, int32_t mode);
 panna_status panna_set_tuning(panna_ctx* ctx, const char* knob, int32_t value);
 
 /*
+ * Langevin dynamics (the MD loop the paper times on a 16-atom carbon cell, Sec. III.B;
+ * the paper names no integrator, read here as BAOAB, Leimkuhler and Matthews):
+ *   B: v += dt/2 F/m;  A: x += dt/2 v;  O: v = c1 v + c2 sqrt(kB T / m) g;  A: x += dt/2 v;
+ *   F = F(x) (panna_energy_forces arithmetic);  B: v += dt/2 F/m;
+ *   c1 = exp(-friction dt), c2 = sqrt(1 - c1^2); temperature 0 and friction 0 give velocity
+ *   Verlet.  g: three normals per atom and step, Box-Muller on the four 32-bit words x of
+ *   Philox4x32-10 (Salmon et al., SC'11) with counter (atom low, atom high, step low, step
+ *   high), key (seed low, seed high), uniforms (x + 1/2) 2^-32; the atom index is the
+ *   global one of the batch, the step index step0 + t.
+ * Every configuration of the batch follows its own trajectory.  Units: A, fs, amu, eV, K
+ * (1 eV/A on 1 amu = 9.648533212e-3 A/fs^2, kB = 8.617333262e-5 eV/K).
+ * Neighbour-list reuse: the neighbour search runs with cutoff rc + skin and is repeated
+ * only when some atom has moved more than skin/2 since the last search (skin 0: every step);
+ * in between, the stored candidates are re-tested at the current positions with the full
+ * search's arithmetic, so the neighbour sets are those of a fresh search.
+ */
+typedef struct {
+    double dt;             /* time step, fs */
+    double temperature;    /* K */
+    double friction;       /* 1/fs */
+    double skin;           /* A */
+    const double* mass;    /* [n_species] amu, host */
+    uint64_t seed;         /* key of the noise stream */
+    int64_t step0;         /* step index of the first step (counter of the noise stream) */
+} panna_md_params;
+
+/*
+ * n_steps of the dynamics above.  sys->pos (device, FP64) is moved in place; vel
+ * [n_atoms*3] FP64 device, A/fs, in/out; F [n_atoms*3] FP32 device in/out: the forces at the
+ * current positions on entry if forces_valid != 0 (else computed first), at the final
+ * positions on exit; E_cfg [n_cfg] FP64 device out: energies at the final positions;
+ * E_traj [n_steps*n_cfg] FP64 device (may be NULL): energies after every step; *n_builds
+ * (host, may be NULL): neighbour searches done.  Synchronous (one small status read per
+ * step).  A neighbour-capacity overflow during the run returns PANNA_ERR_NEIGHBOR_OVERFLOW
+ * with positions and velocities advanced to that step (raise the capacity and restart from
+ * a copy); ghost atoms are rejected (PANNA_ERR_UNSUPPORTED).
+ */
+panna_status panna_md_run(panna_ctx* ctx, const panna_system* sys, double* vel, const float* theta,
+                          int32_t mlp_precision, const panna_md_params* params, int64_t n_steps,
+                          float* F, int32_t forces_valid, double* E_cfg, double* E_traj,
+                          int64_t* n_builds, panna_stream_t stream);
+
+/*
  * Normalisers of the training loss (Sec. II.A): with n_cfg_total > 0 and n_atoms_total > 0,
  * panna_loss_grad divides the energy term by n_cfg_total and the force term by
  * 3 * n_atoms_total instead of the batch's own counts.  In data-parallel training each

@@ -6,6 +6,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <string>
 
 #include "common.cuh"
@@ -72,6 +74,7 @@ struct panna_ctx {
     DescDev d{};
     MlpPlan plan{};
     int32_t cap = 64;
+    int32_t cap_c = 0;                // dynamics: candidate slots per atom (cutoff rc + skin)
     int async = 0;
     int profiling = 0;
     int ang_mode = 0;
@@ -121,6 +124,11 @@ struct Layout {
     double* loss_part = nullptr;
     void* tc_ws = nullptr;   // BF16 tensor-core network buffers
     void* tf_ws = nullptr;   // FP32 networks: TF32 first-layer buffers
+    // dynamics: candidates of the last neighbour build (cutoff rc + skin), its positions
+    int32_t* cand_count = nullptr;
+    float4* cand_vec = nullptr;
+    int2* cand_idx = nullptr;
+    double* pos_ref = nullptr;
 };
 
 constexpr int kSplits = 16;
@@ -132,7 +140,7 @@ int tf32_mask(const panna_ctx* c, bool bf16, bool train)
     return c->fp32_tc & (train ? (TF32_FWD | TF32_INGRAD | TF32_TAN | TF32_WGRAD) : (TF32_FWD | TF32_INGRAD));
 }
 
-void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, Layout& L)
+void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, Layout& L, int cap_c = 0)
 {
     const int S = c->d.S, D = c->d.D, cap = c->cap;
     const MlpPlan& p = c->plan;
@@ -180,6 +188,12 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, 
     b.splits = kSplits;
     if (bf16) L.tc_ws = a.take<char>(tc_workspace_bytes(p, N, true));
     if (const int m = tf32_mask(c, bf16, train)) L.tf_ws = a.take<char>(tf32_workspace_bytes(p, N, m));
+    if (cap_c > 0) {
+        L.cand_count = a.take<int32_t>(N);
+        L.cand_vec = a.take<float4>((size_t)N * cap_c);
+        L.cand_idx = a.take<int2>((size_t)N * cap_c);
+        L.pos_ref = a.take<double>(3 * (size_t)N);
+    }
     if (train) {
         for (int l = 1; l <= p.L; ++l) {
             b.Zd[l] = a.take<float>((size_t)N * p.ld[l]);
@@ -197,12 +211,13 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, 
     }
 }
 
-panna_status prepare(panna_ctx* c, const panna_system* sys, bool train, bool bf16, Layout& L, cudaStream_t s)
+panna_status prepare(panna_ctx* c, const panna_system* sys, bool train, bool bf16, Layout& L, cudaStream_t s,
+                     int cap_c = 0)
 {
     const int64_t N = sys->n_atoms, C = sys->n_cfg;
     Arena sz;
     sz.sizing = true;
-    carve(c, sz, N, C, train, bf16, L);
+    carve(c, sz, N, C, train, bf16, L, cap_c);
     if (sz.off > c->ws.cap) {
         if (c->ws.base) {
             CU(cudaStreamSynchronize(s));
@@ -221,7 +236,7 @@ panna_status prepare(panna_ctx* c, const panna_system* sys, bool train, bool bf1
     Arena real = c->ws;
     real.sizing = false;
     real.off = 0;
-    carve(c, real, N, C, train, bf16, L);
+    carve(c, real, N, C, train, bf16, L, cap_c);
     L.w.sys = sys;
     return PANNA_OK;
 }
@@ -295,6 +310,7 @@ struct Request {
     const double* dE = nullptr;
     const float* dF = nullptr;
     float* dtheta = nullptr;
+    const Work* cand = nullptr;  // dynamics: refresh these candidates instead of a neighbour search
 };
 
 // Kernel variants (0 blocked, 1 flattened) of the descriptor-family kernels for this problem
@@ -345,7 +361,8 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     c->n_marked = 0;
     CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
     stage_mark(c, 0, s);
-    CU(build_neighbors(L.w, c->d, s, &nl));
+    if (rq.cand) CU(refresh_neighbors(*rq.cand, L.w, c->d, s, &nl));
+    else CU(build_neighbors(L.w, c->d, s, &nl));
     if (rq.G_out) {
         stage_mark(c, 1, s);
         CU(launch_descriptor(L.w, c->d, rq.G_out, nullptr, c->ang_mode != 2, s, &nl));
@@ -461,6 +478,38 @@ panna_status run(panna_ctx* c, const panna_system* sys, const Request& rq, cudaS
         return st;
     }
     return PANNA_OK;
+}
+
+// ------------------------------------------------------------------ dynamics
+
+constexpr double kMdAcc = 9.648533212e-3;   // (eV/A)/amu in A/fs^2
+constexpr double kMdKb = 8.617333262e-5;    // eV/K
+
+// candidates of a neighbour search with cutoff rc + skin into L.cand_*, positions recorded
+panna_status md_build(panna_ctx* c, const panna_system* sys, Layout& L, Work& wc, double skin, cudaStream_t s)
+{
+    wc = L.w;
+    wc.nb_count = L.cand_count;
+    wc.nb_vec = L.cand_vec;
+    wc.nb_idx = L.cand_idx;
+    wc.cap = c->cap_c;
+    DescDev dc = c->d;
+    dc.rc_d = c->d.rc_d + skin;
+    dc.rc = (float)dc.rc_d;
+    int nl = 0;
+    CU(build_neighbors(wc, dc, s, &nl));
+    CU(cudaMemcpyAsync(L.pos_ref, sys->pos, sizeof(double) * 3 * (size_t)sys->n_atoms, cudaMemcpyDeviceToDevice, s));
+    return PANNA_OK;
+}
+
+// reads the status word (one copy, one synchronisation)
+panna_status md_status(panna_ctx* c, const Layout& L, cudaStream_t s, bool* stale, int* need)
+{
+    CU(cudaMemcpyAsync(c->h_status, L.w.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    *stale = c->h_status->stale != 0;
+    *need = c->h_status->need_cap;
+    return (panna_status)c->h_status->code;
 }
 
 }  // namespace
@@ -622,6 +671,82 @@ panna_status panna_set_tuning(panna_ctx* c, const char* knob, int32_t value)
         return PANNA_OK;
     }
     return fail(PANNA_ERR_INVALID_ARG, "unknown tuning knob or value: %s=%d", knob, value);
+}
+
+panna_status panna_md_run(panna_ctx* c, const panna_system* sys, double* vel, const float* theta, int32_t prec,
+                          const panna_md_params* p, int64_t n_steps, float* F, int32_t forces_valid, double* E_cfg,
+                          double* E_traj, int64_t* n_builds, panna_stream_t stream)
+{
+    ST(check_system(c, sys));
+    if (!vel || !theta || !p || !F || !E_cfg || !p->mass || n_steps < 0)
+        return fail(PANNA_ERR_INVALID_ARG, "vel, theta, params (with masses), F and E_cfg are required");
+    if (!(p->dt > 0.0) || !(p->temperature >= 0.0) || !(p->friction >= 0.0) || !(p->skin >= 0.0))
+        return fail(PANNA_ERR_INVALID_ARG, "dt must be > 0; temperature, friction and skin >= 0");
+    if (prec < PANNA_MLP_FP32 || prec > PANNA_MLP_BF16_FAST) return fail(PANNA_ERR_INVALID_ARG, "unknown precision");
+    if (sys->ghost) return fail(PANNA_ERR_UNSUPPORTED, "dynamics of a batch with ghost atoms");
+    MdSpecies ms{};
+    for (int sp = 0; sp < c->d.S; ++sp) {
+        if (!(p->mass[sp] > 0.0)) return fail(PANNA_ERR_INVALID_ARG, "mass of species %d must be > 0", sp);
+        ms.acc[sp] = kMdAcc / p->mass[sp];
+        ms.sigma[sp] = sqrt(kMdKb * p->temperature * ms.acc[sp]);
+    }
+    CU(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = sys->n_atoms;
+    double* pos = const_cast<double*>(sys->pos);     // the dynamics moves the caller's positions
+    const double c1 = exp(-p->friction * p->dt), c2 = sqrt(fmax(0.0, 1.0 - c1 * c1));
+    const int thermostat = (p->friction > 0.0 || p->temperature > 0.0) ? 1 : 0;
+    const double lim2 = 0.25 * p->skin * p->skin;
+    const bool bf16 = prec != PANNA_MLP_FP32;
+    const double grow = (c->d.rc_d + p->skin) / c->d.rc_d;
+    c->cap_c = std::max<int32_t>(c->cap_c, (int32_t)(c->cap * grow * grow * grow) + 8);
+    Request rq;
+    rq.theta = theta; rq.prec = prec; rq.E_cfg = E_cfg; rq.F = F; rq.forces = true; rq.energy = true;
+    Layout L;
+    Work wc{};
+    bool stale = false;
+    int need = 0;
+    int64_t builds = 0;
+    // first neighbour build, and the forces at the starting positions; capacities grow here
+    for (int attempt = 0;; ++attempt) {
+        ST(prepare(c, sys, false, bf16, L, s, c->cap_c));
+        CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
+        ST(md_build(c, sys, L, wc, p->skin, s));
+        panna_status st = md_status(c, L, s, &stale, &need);
+        if (st == PANNA_ERR_NEIGHBOR_OVERFLOW && attempt < 3) { c->cap_c = need + need / 4 + 8; continue; }
+        if (st != PANNA_OK) return collect(c, L, s, &need);
+        rq.cand = &wc;
+        c->last_launches = 0;
+        if (!forces_valid || attempt > 0) {
+            ST(run_once(c, sys, rq, L, s));
+            st = md_status(c, L, s, &stale, &need);
+            if (st == PANNA_ERR_NEIGHBOR_OVERFLOW && attempt < 3) { c->cap = need + need / 4 + 8; continue; }
+            if (st != PANNA_OK) return collect(c, L, s, &need);
+        }
+        ++builds;
+        break;
+    }
+    for (int64_t t = 0; t < n_steps; ++t) {
+        CU(launch_md_baoa(N, sys->species, ms, pos, vel, F, p->dt, c1, c2, thermostat, p->seed, p->step0 + t,
+                          L.pos_ref, lim2, &L.w.status->stale, s));
+        const panna_status st = md_status(c, L, s, &stale, &need);
+        if (st != PANNA_OK) {
+            collect(c, L, s, &need);
+            return fail(st, "step %lld: %s (raise the neighbour capacity and restart)", (long long)t,
+                        panna_last_error());
+        }
+        if (stale || p->skin == 0.0) {
+            ST(md_build(c, sys, L, wc, p->skin, s));
+            ++builds;
+        }
+        ST(run_once(c, sys, rq, L, s));
+        CU(launch_md_b(N, sys->species, ms, vel, F, p->dt, s));
+        if (E_traj)
+            CU(cudaMemcpyAsync(E_traj + t * sys->n_cfg, E_cfg, sizeof(double) * (size_t)sys->n_cfg,
+                               cudaMemcpyDeviceToDevice, s));
+    }
+    if (n_builds) *n_builds = builds;
+    return collect(c, L, s, &need);
 }
 
 panna_status panna_set_loss_normalization(panna_ctx* c, int64_t n_cfg_total, int64_t n_atoms_total)

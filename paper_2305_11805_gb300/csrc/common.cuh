@@ -17,7 +17,7 @@ struct DevStatus {
     int32_t code;
     int32_t need_cap;
     int32_t bad_index;
-    int32_t pad;
+    int32_t stale;      // dynamics: an atom moved more than skin/2 since the neighbour build
 };
 
 __device__ __forceinline__ void set_status(DevStatus* st, int32_t code, int32_t idx)
@@ -102,6 +102,9 @@ int64_t scan_scratch_elems(int64_t n);
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s, int* launches);
 cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* launches);
 cudaError_t species_order(Work& w, int S, cudaStream_t s, int* launches);
+// Verlet list: `cand` holds the candidates of a build with cutoff rc + skin (its nb_count,
+// nb_idx, cap); writes w's neighbour slots for cutoff d.rc at the current positions
+cudaError_t refresh_neighbors(const Work& cand, Work& w, const DescDev& d, cudaStream_t s, int* launches);
 cudaError_t export_neighbors(const Work& w, int64_t* off, int64_t* nbr_j, int32_t* shift, int64_t cap_total, cudaStream_t s, int* launches);
 
 // descriptor family (descriptor.cu); row_map == nullptr writes row i for atom i
@@ -115,6 +118,15 @@ cudaError_t launch_adjoint(const Work& w, const DescDev& d, const float* g_rows,
                            int variant, cudaStream_t s, int* launches);
 cudaError_t launch_jvp(const Work& w, const DescDev& d, const float* u, float* wdot_rows, bool acc, cudaStream_t s,
                        int* launches, int variant = 0);
+
+// Langevin dynamics (md.cu): per species a = (eV/A)/m in A/fs^2 and the thermal velocity
+// scale sigma = sqrt(kB T a) in A/fs
+struct MdSpecies { double acc[kMaxSpecies]; double sigma[kMaxSpecies]; };
+cudaError_t launch_md_baoa(int64_t N, const int32_t* species, const MdSpecies& ms, double* pos, double* vel,
+                           const float* F, double dt, double c1, double c2, int thermostat, uint64_t seed,
+                           int64_t step, const double* pos_ref, double lim2, int32_t* stale, cudaStream_t s);
+cudaError_t launch_md_b(int64_t N, const int32_t* species, const MdSpecies& ms, double* vel, const float* F,
+                        double dt, cudaStream_t s);
 
 // reductions (reduce.cu)
 int cfg_chunks(int64_t N, int64_t C);

@@ -493,6 +493,106 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
     }
 }
 
+// ------------------------------------------------------------------ Verlet-list refresh
+
+// Positions folded with the lattice offsets recorded when the list was built (wrap), so the
+// image shifts stored with the candidates stay valid while atoms move; species in .w kept.
+__global__ void k_fold_frozen(int64_t N, const double* __restrict__ pos, const int32_t* __restrict__ atom_cfg,
+                              const CfgGeom* __restrict__ geom, const int32_t* __restrict__ wrap,
+                              float4* __restrict__ pos_hi, float4* __restrict__ pos_lo)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const CfgGeom& g = geom[atom_cfg[i]];
+    const int m0 = wrap[3 * i], m1 = wrap[3 * i + 1], m2 = wrap[3 * i + 2];
+    double xw[3];
+    for (int d = 0; d < 3; ++d) xw[d] = pos[3 * i + d] + m0 * g.cell[d] + m1 * g.cell[3 + d] + m2 * g.cell[6 + d];
+    const float h0 = (float)xw[0], h1 = (float)xw[1], h2 = (float)xw[2];
+    const float w = pos_hi[i].w;
+    pos_hi[i] = make_float4(h0, h1, h2, w);
+    pos_lo[i] = make_float4((float)(xw[0] - h0), (float)(xw[1] - h1), (float)(xw[2] - h2), 0.f);
+}
+
+// The candidates (j, image) found within rc + skin when the list was built are re-tested
+// at the current positions with the arithmetic of the full search (FP32 band filter,
+// double-float relative vector, FP64 re-test near rc); those with r < rc are kept in their
+// stored order (grouped by species).  Exact as long as no atom has moved more than skin/2
+// since the build (every pair now within rc was then within rc + skin).
+__global__ void __launch_bounds__(kNbWarps * 32)
+k_refresh(int64_t N, double rc_d, float rc, const CfgGeom* __restrict__ geom, const int32_t* __restrict__ atom_cfg,
+          const int32_t* __restrict__ cand_count, const int2* __restrict__ cand_idx, int cap_c,
+          const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo, int cap,
+          int32_t* __restrict__ nb_count, float4* __restrict__ nb_vec, int2* __restrict__ nb_idx, DevStatus* st)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kNbWarps + warp;
+    if (i >= N) return;
+    const CfgGeom& g = geom[atom_cfg[i]];
+    const float4 xih = pos_hi[i], xil = pos_lo[i];
+    const float band = rc + 1e-2f, band2 = band * band, rc2 = rc * rc;
+    const double rc2d = rc_d * rc_d;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nc = min(cand_count[i], cap_c);
+    const size_t cin = (size_t)i * cap_c, out = (size_t)i * cap;
+    int count = 0;
+    for (int base = 0; base < nc; base += 32) {
+        const int k = base + lane;
+        bool in = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        int2 e = make_int2(0, 0);
+        if (k < nc) {
+            e = cand_idx[cin + k];
+            const int t0 = meta_t(e.y, 0), t1 = meta_t(e.y, 1), t2 = meta_t(e.y, 2);
+            float shh[3], shl[3];
+            if (t0 >= -1 && t0 <= 1 && t1 >= -1 && t1 <= 1 && t2 >= -1 && t2 <= 1) {
+                const int q = (t0 + 1) * 9 + (t1 + 1) * 3 + (t2 + 1);
+                for (int d = 0; d < 3; ++d) { shh[d] = g.sh_hi[q][d]; shl[d] = g.sh_lo[q][d]; }
+            } else {
+                shift_hilo(g, t0, t1, t2, shh, shl);
+            }
+            const float4 xjh = pos_hi[e.x];
+            const float fx = (xjh.x + shh[0]) - xih.x, fy = (xjh.y + shh[1]) - xih.y, fz = (xjh.z + shh[2]) - xih.z;
+            if (fx * fx + fy * fy + fz * fz < band2) {
+                const float4 xjl = pos_lo[e.x];
+                dx = dd_rel(xjh.x, xjl.x, shh[0], shl[0], xih.x, xil.x);
+                dy = dd_rel(xjh.y, xjl.y, shh[1], shl[1], xih.y, xil.y);
+                dz = dd_rel(xjh.z, xjl.z, shh[2], shl[2], xih.z, xil.z);
+                r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+                if (fabsf(r2 - rc2) <= 2e-6f * rc2) in = retest_fp64(xjh, xjl, shh, shl, xih, xil, rc2d);
+                else in = r2 < rc2;
+                if (in && r2 == 0.f) { set_status(st, PANNA_ERR_BAD_INPUT, (int)i); in = false; }
+            }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int p = count + __popc(mask & lt);
+            if (p < cap) {
+                nb_vec[out + p] = make_float4(dx, dy, dz, sqrtf(r2));
+                nb_idx[out + p] = e;
+            }
+        }
+        count += __popc(mask);
+    }
+    if (count > cap && lane == 0) {
+        atomicMax(&st->need_cap, count);
+        set_status(st, PANNA_ERR_NEIGHBOR_OVERFLOW, (int)i);
+    }
+    if (lane == 0) nb_count[i] = count < cap ? count : cap;
+}
+
+cudaError_t refresh_neighbors(const Work& cand, Work& w, const DescDev& d, cudaStream_t s, int* launches)
+{
+    const int64_t N = w.N;
+    if (N == 0) return cudaSuccess;
+    k_fold_frozen<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, w.sys->pos, w.atom_cfg, w.geom, w.wrap, w.pos_hi,
+                                                              w.pos_lo);
+    k_refresh<<<(unsigned)((N + kNbWarps - 1) / kNbWarps), kNbWarps * 32, 0, s>>>(
+        N, d.rc_d, d.rc, w.geom, w.atom_cfg, cand.nb_count, cand.nb_idx, cand.cap, w.pos_hi, w.pos_lo, w.cap,
+        w.nb_count, w.nb_vec, w.nb_idx, w.status);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ CSR export
 
 __global__ void k_count_i64(int64_t N, const int32_t* __restrict__ cnt, int64_t* __restrict__ out)

@@ -46,6 +46,11 @@ class panna_system(C.Structure):
                 ("species", _vp), ("cell", _vp), ("pbc", _vp), ("ghost", _vp)]
 
 
+class panna_md_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("temperature", C.c_double), ("friction", C.c_double), ("skin", C.c_double),
+                ("mass", C.POINTER(C.c_double)), ("seed", C.c_uint64), ("step0", C.c_int64)]
+
+
 class PannaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("panna status %d: %s" % (status, msg))
@@ -79,6 +84,8 @@ def load(path: str = LIB_PATH):
         "panna_set_angular_precision": (i32, [_vp, i32]),
         "panna_set_tuning": (i32, [_vp, C.c_char_p, i32]),
         "panna_set_loss_normalization": (i32, [_vp, i64, i64]),
+        "panna_md_run": (i32, [_vp, C.POINTER(panna_system), _vp, _vp, i32, C.POINTER(panna_md_params), i64, _vp,
+                               i32, _vp, _vp, C.POINTER(i64), _vp]),
         "panna_neighbors": (i32, [_vp, C.POINTER(panna_system), i64, _vp, _vp, _vp, C.POINTER(i64), _vp]),
         "panna_descriptors": (i32, [_vp, C.POINTER(panna_system), _vp, _vp]),
         "panna_energy_forces": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
@@ -103,6 +110,7 @@ def exported_symbols() -> Sequence[str]:
     return ["panna_version", "panna_last_error", "panna_descriptor_size", "panna_create", "panna_destroy",
             "panna_param_count", "panna_set_neighbor_capacity", "panna_neighbor_capacity", "panna_set_async",
             "panna_check", "panna_set_angular_precision", "panna_set_tuning", "panna_set_loss_normalization",
+            "panna_md_run",
             "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
             "panna_descriptors_static", "panna_capture", "panna_replay"]
@@ -188,6 +196,21 @@ def panna_set_tuning(ctx: int, knob: str, value: int):
 
 def panna_set_loss_normalization(ctx: int, n_cfg_total: int, n_atoms_total: int):
     _check(load().panna_set_loss_normalization(ctx, int(n_cfg_total), int(n_atoms_total)))
+
+
+def panna_md_run(ctx: int, sysd: "DeviceSystem", vel, theta, prec: int, dt: float, temperature: float,
+                 friction: float, skin: float, mass, seed: int, step0: int, n_steps: int, F, forces_valid: bool,
+                 E_cfg, E_traj=None, stream=None) -> int:
+    """Langevin dynamics (see the header); moves sysd.pos in place, returns the number of
+    neighbour searches."""
+    m = (C.c_double * len(mass))(*[float(x) for x in mass])
+    prm = panna_md_params(float(dt), float(temperature), float(friction), float(skin),
+                          C.cast(m, C.POINTER(C.c_double)), int(seed), int(step0))
+    nb = C.c_int64(0)
+    _check(load().panna_md_run(ctx, C.byref(sysd.s), _ptr(vel), _ptr(theta), int(prec), C.byref(prm), int(n_steps),
+                               _ptr(F), 1 if forces_valid else 0, _ptr(E_cfg), _ptr(E_traj), C.byref(nb),
+                               _stream(stream)))
+    return int(nb.value)
 
 
 def panna_check(ctx: int, stream=None):
