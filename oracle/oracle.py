@@ -69,7 +69,10 @@ def lib():
         L.orc_batch.restype = C.c_int
         L.orc_batch.argtypes = [C.c_int64, _i64p, _dp, _i32p, _dp, _u8p, C.POINTER(OrcDesc),
                                 C.POINTER(OrcArch), _dp, _i64p, _dp, _dp, _dp, _dp, _dp,
-                                _dp, _dp, C.c_double, _dp, _dp, _u8p, C.c_double, C.c_double]
+                                _dp, _dp, C.c_double, _dp, _dp, _u8p, C.c_double, C.c_double, C.POINTER(OrcLoss)]
+        L.orc_adam_step.restype = None
+        L.orc_adam_step.argtypes = [C.c_int64, _dp, _dp, _dp, _dp, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, C.c_double, C.c_double, _u8p]
         L.orc_sampled.restype = C.c_int
         L.orc_sampled.argtypes = [C.c_int64, _dp, _i32p, _dp, _u8p, C.POINTER(OrcDesc),
                                   C.POINTER(OrcArch), _dp, _i64p, C.c_int64, _i64p, C.c_int64,
@@ -84,6 +87,11 @@ def lib():
                                    C.c_double, C.c_uint64, C.c_int64, C.c_int64, _dp, _dp]
         _lib = L
     return _lib
+
+
+class OrcLoss(C.Structure):
+    _fields_ = [("e_kind", C.c_int32), ("f_kind", C.c_int32), ("e_per_atom", C.c_int32),
+                ("l1", C.c_double), ("l2", C.c_double)]
 
 
 def _ptr(a: Optional[np.ndarray], t):
@@ -186,11 +194,12 @@ def neighbor_list(system, rc: float):
 
 
 def batch(system, desc, archs, theta, want_G: bool = False, e_ref=None, f_ref=None,
-          w_force: float = 0.1, param_grad: bool = False, ghost=None, norm=None):
+          w_force: float = 0.1, param_grad: bool = False, ghost=None, norm=None, loss_options=None):
     """Whole-batch FP64 evaluation; returns a dict of numpy arrays (see orc_batch).
 
     ghost: optional [n_atoms] flags of atoms that are neighbours only (not centres).
-    norm: optional (C, N) loss normalisers replacing the batch's own counts."""
+    norm: optional (C, N) loss normalisers replacing the batch's own counts.
+    loss_options: optional dict(e_kind, f_kind (0 quadratic, 1 exponential), e_per_atom, l1, l2)."""
     s = system
     h = _DescHolder(desc)
     D = lib().orc_descriptor_size(C.byref(h.s))
@@ -210,12 +219,18 @@ def batch(system, desc, archs, theta, want_G: bool = False, e_ref=None, f_ref=No
     loss = np.zeros(1)
     dth = np.zeros(len(th)) if (param_grad and er is not None) else None
     gh = None if ghost is None else np.ascontiguousarray(ghost, np.uint8)
+    lo = None
+    if loss_options is not None:
+        o = dict(e_kind=0, f_kind=0, e_per_atom=0, l1=0.0, l2=0.0)
+        o.update(loss_options)
+        lo = OrcLoss(int(o["e_kind"]), int(o["f_kind"]), int(o["e_per_atom"]), float(o["l1"]), float(o["l2"]))
     lib().orc_batch(Cn, _ptr(off, _i64p), _ptr(pos, _dp), _ptr(spec, _i32p), _ptr(cell, _dp),
                     _ptr(pbc, _u8p), C.byref(h.s), arr, _ptr(th, _dp), _ptr(toff, _i64p),
                     _ptr(G, _dp), _ptr(out["E_atom"], _dp), _ptr(out["E_cfg"], _dp),
                     _ptr(out["F"], _dp), _ptr(out["virial"], _dp), _ptr(er, _dp), _ptr(fr, _dp),
                     float(w_force), _ptr(loss, _dp), _ptr(dth, _dp), _ptr(gh, _u8p),
-                    float(norm[0]) if norm else 0.0, float(norm[1]) if norm else 0.0)
+                    float(norm[0]) if norm else 0.0, float(norm[1]) if norm else 0.0,
+                    C.byref(lo) if lo is not None else None)
     if want_G:
         out["G"] = G
     if er is not None:
@@ -229,6 +244,18 @@ def workload_batch(wl, want_G=False, train=False):
     return batch(wl.system, wl.desc, wl.archs, wl.theta, want_G=want_G,
                  e_ref=wl.e_ref if train else None, f_ref=wl.f_ref if train else None,
                  w_force=wl.w_force, param_grad=train)
+
+
+def adam_step(theta, grad, m, v, t, lr0, rate=1.0, steps=0.0, b1=0.9, b2=0.999, eps=1e-8, frozen=None):
+    """One FP64 Adam step (see orc_adam_step); returns new (theta, m, v)."""
+    th = np.array(theta, np.float64, copy=True)
+    mm = np.array(m, np.float64, copy=True)
+    vv = np.array(v, np.float64, copy=True)
+    g = np.ascontiguousarray(grad, np.float64)
+    fr = None if frozen is None else np.ascontiguousarray(frozen, np.uint8)
+    lib().orc_adam_step(len(th), _ptr(th, _dp), _ptr(g, _dp), _ptr(mm, _dp), _ptr(vv, _dp), int(t), float(lr0),
+                        float(rate), float(steps), float(b1), float(b2), float(eps), _ptr(fr, _u8p))
+    return th, mm, vv
 
 
 def philox4x32_10(ctr, key):

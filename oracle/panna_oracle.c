@@ -510,13 +510,25 @@ static void work_free(orc_work* wk)
  *   dL/dtheta = sum_i d/dtheta [ alpha_c(i) E_i - g_i . w_i ].
  * Returns 0.
  */
+/* Loss options of Sec. II.A: for the energy and the force terms a quadratic x^2 or an
+ * exponential exp(x^2) - 1 function of the difference (the paper names both, without the
+ * form; this reading equals the quadratic to leading order), energies per configuration or
+ * per atom (difference divided by the configuration's atom count), and a penalty
+ * l1 sum |w| + l2 sum w^2 over every weight (biases excluded). */
+typedef struct { int32_t e_kind, f_kind, e_per_atom; double l1, l2; } orc_loss;
+
+static double loss_term(int kind, double x) { return kind ? exp(x * x) - 1.0 : x * x; }
+static double loss_slope(int kind, double x) { return kind ? 2.0 * x * exp(x * x) : 2.0 * x; }
+
 int orc_batch(int64_t n_cfg, const int64_t* atom_off, const double* pos, const int32_t* species,
               const double* cell, const uint8_t* pbc, const orc_desc* p, const orc_arch* archs,
               const double* theta, const int64_t* theta_off,
               double* G_out, double* E_atom, double* E_cfg, double* F, double* virial,
               const double* E_ref, const double* F_ref, double w_force, double* loss, double* dtheta,
-              const uint8_t* ghost, double c_norm, double n_norm)
+              const uint8_t* ghost, double c_norm, double n_norm, const orc_loss* lo)
 {
+    const orc_loss lq = {0, 0, 0, 0.0, 0.0};
+    if (!lo) lo = &lq;
     const int D = orc_descriptor_size(p);
     const int64_t N = atom_off[n_cfg];
     /* Loss normalisers: the batch's own counts unless given (a shard of a larger batch). */
@@ -572,19 +584,33 @@ int orc_batch(int64_t n_cfg, const int64_t* atom_off, const double* pos, const i
     }
 
     if (E_ref) {
-        double le = 0.0, lf = 0.0;
-        for (int64_t c = 0; c < n_cfg; ++c) le += (E_cfg[c] - E_ref[c]) * (E_cfg[c] - E_ref[c]);
-        for (int64_t t = 0; t < 3 * N; ++t) lf += (F[t] - F_ref[t]) * (F[t] - F_ref[t]);
-        *loss = le / CN + w_force * lf / (3.0 * NN);
+        double le = 0.0, lf = 0.0, l1 = 0.0, l2 = 0.0;
+        for (int64_t c = 0; c < n_cfg; ++c) {
+            const int64_t n = atom_off[c + 1] - atom_off[c];
+            double d = E_cfg[c] - E_ref[c];
+            if (lo->e_per_atom && n > 0) d /= (double)n;
+            le += loss_term(lo->e_kind, d);
+        }
+        for (int64_t t = 0; t < 3 * N; ++t) lf += loss_term(lo->f_kind, F[t] - F_ref[t]);
+        const int S = p->n_species;
+        for (int s = 0; s < S; ++s) {           /* weights of every layer, biases excluded */
+            int64_t off = theta_off[s];
+            for (int l = 0; l < archs[s].n_layers; ++l) {
+                const int64_t nw = (int64_t)archs[s].widths[l + 1] * archs[s].widths[l];
+                for (int64_t k = 0; k < nw; ++k) { l1 += fabs(theta[off + k]); l2 += theta[off + k] * theta[off + k]; }
+                off += nw + archs[s].widths[l + 1];
+            }
+        }
+        *loss = le / CN + w_force * lf / (3.0 * NN) + lo->l1 * l1 + lo->l2 * l2;
         if (dtheta) {
-            int S = p->n_species;
             memset(dtheta, 0, sizeof(double) * theta_off[S]);
             double* u = (double*)malloc(sizeof(double) * 3 * N);
-            for (int64_t t = 0; t < 3 * N; ++t) u[t] = 2.0 * w_force / (3.0 * NN) * (F[t] - F_ref[t]);
+            for (int64_t t = 0; t < 3 * N; ++t) u[t] = w_force / (3.0 * NN) * loss_slope(lo->f_kind, F[t] - F_ref[t]);
             for (int64_t c = 0; c < n_cfg; ++c) {
                 int64_t a0 = atom_off[c], n = atom_off[c + 1] - a0;
                 const double* cp = cell + 9 * c; const uint8_t* pp = pbc + 3 * c;
-                double alpha = 2.0 / CN * (E_cfg[c] - E_ref[c]);
+                const double per = (lo->e_per_atom && n > 0) ? 1.0 / (double)n : 1.0;
+                double alpha = loss_slope(lo->e_kind, (E_cfg[c] - E_ref[c]) * per) * per / CN;
                 for (int64_t i = 0; i < n; ++i) {
                     if (ghost && ghost[a0 + i]) continue;
                     int64_t k = env(i, n, pos + 3 * a0, species + a0, cp, pp, p->rc, NULL, 0, &wk.nb, &wk.cap);
@@ -608,10 +634,38 @@ int orc_batch(int64_t n_cfg, const int64_t* atom_off, const double* pos, const i
                 }
             }
             free(u);
+            for (int s = 0; s < S; ++s) {       /* penalty gradient: l1 sign(w) + 2 l2 w */
+                int64_t off = theta_off[s];
+                for (int l = 0; l < archs[s].n_layers; ++l) {
+                    const int64_t nw = (int64_t)archs[s].widths[l + 1] * archs[s].widths[l];
+                    for (int64_t k = 0; k < nw; ++k) {
+                        const double w = theta[off + k];
+                        dtheta[off + k] += lo->l1 * ((w > 0.0) - (w < 0.0)) + 2.0 * lo->l2 * w;
+                    }
+                    off += nw + archs[s].widths[l + 1];
+                }
+            }
         }
     }
     work_free(&wk);
     return 0;
+}
+
+/* One Adam step (Kingma and Ba, Algorithm 1) for step t >= 1: m = b1 m + (1 - b1) g,
+ * v = b2 v + (1 - b2) g^2, theta -= lr_t (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+ * with lr_t = lr0 rate^(t / steps) (exponential decay; steps = 0: constant).  Entries with
+ * frozen[k] != 0 keep theta, m and v. */
+void orc_adam_step(int64_t n, double* theta, const double* g, double* m, double* v, int64_t t, double lr0,
+                   double rate, double steps, double b1, double b2, double eps, const uint8_t* frozen)
+{
+    const double lr = steps > 0.0 ? lr0 * pow(rate, (double)t / steps) : lr0;
+    const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (int64_t k = 0; k < n; ++k) {
+        if (frozen && frozen[k]) continue;
+        m[k] = b1 * m[k] + (1.0 - b1) * g[k];
+        v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
+        theta[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);
+    }
 }
 
 /*
@@ -763,7 +817,7 @@ int orc_md_baoab(int64_t n_cfg, const int64_t* atom_off, double* pos, double* ve
     double* E_atom = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
     double* E_cfg = (double*)malloc(sizeof(double) * (size_t)n_cfg);
     orc_batch(n_cfg, atom_off, pos, species, cell, pbc, p, archs, theta, theta_off, NULL, E_atom, E_cfg, F, NULL,
-              NULL, NULL, 0.0, NULL, NULL, NULL, 0.0, 0.0);
+              NULL, NULL, 0.0, NULL, NULL, NULL, 0.0, 0.0, NULL);
     const double c1 = exp(-friction * dt), c2 = sqrt(1.0 - c1 * c1);
     const int thermostat = friction > 0.0 || temperature > 0.0;
     for (int64_t t = 0; t < n_steps; ++t) {
@@ -782,7 +836,7 @@ int orc_md_baoab(int64_t n_cfg, const int64_t* atom_off, double* pos, double* ve
             }
         }
         orc_batch(n_cfg, atom_off, pos, species, cell, pbc, p, archs, theta, theta_off, NULL, E_atom, E_cfg, F,
-                  NULL, NULL, NULL, 0.0, NULL, NULL, NULL, 0.0, 0.0);
+                  NULL, NULL, NULL, 0.0, NULL, NULL, NULL, 0.0, 0.0, NULL);
         for (int64_t i = 0; i < N; ++i) {
             const double a = ORC_ACC / mass[species[i]];
             for (int d = 0; d < 3; ++d) vel[3 * i + d] += 0.5 * dt * F[3 * i + d] * a;
