@@ -265,6 +265,52 @@ panna_status panna_md_run(panna_ctx* ctx, const panna_system* sys, double* vel, 
  */
 panna_status panna_set_loss_normalization(panna_ctx* ctx, int64_t n_cfg_total, int64_t n_atoms_total);
 
+/*
+ * Loss options of Sec. II.A (the paper names the choices; the exponential form is read as
+ * exp(x^2) - 1, equal to the quadratic to leading order):
+ *   L = (1/C) sum_c l_E(d_c) + w_force/(3N) sum_{m,a} l_F(F_ma - F_ref_ma)
+ *       + l1 sum |w| + l2 sum w^2,
+ * l(x) = x^2 (PANNA_LOSS_QUADRATIC) or exp(x^2) - 1 (PANNA_LOSS_EXPONENTIAL),
+ * d_c = E_c - E_ref_c, or (E_c - E_ref_c) / n_c with energy_per_atom, the penalty over every
+ * weight of every layer and species (biases excluded; the sign of 0 is 0).  Applies to
+ * panna_loss_grad.  NULL restores the default (quadratic, per configuration, no penalty).
+ * The exponential terms suit small residuals (per-atom energies, a trained model).
+ */
+#define PANNA_LOSS_QUADRATIC 0
+#define PANNA_LOSS_EXPONENTIAL 1
+typedef struct {
+    int32_t energy_loss;
+    int32_t force_loss;
+    int32_t energy_per_atom;
+    double l1;
+    double l2;
+} panna_loss_options;
+panna_status panna_set_loss_options(panna_ctx* ctx, const panna_loss_options* options);
+
+/*
+ * Adam (Sec. II.A; Kingma and Ba, Algorithm 1) on the flat parameter vector, one fused pass:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   theta -= lr_t (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+ *   lr_t = lr decay_rate^(t / decay_steps) (exponential decay; decay_steps 0: constant).
+ * theta, grad, m, v: [P] FP32 device (m, v zero before step t = 1); t >= 1.  Parameters of
+ * layers frozen with panna_set_frozen keep theta, m and v (fine tuning, transfer learning).
+ * Asynchronous on `stream`.
+ */
+typedef struct {
+    double lr;
+    double beta1;
+    double beta2;
+    double eps;
+    double decay_rate;
+    double decay_steps;
+} panna_adam_params;
+panna_status panna_adam_step(panna_ctx* ctx, float* theta, const float* grad, float* m, float* v, int64_t t,
+                             const panna_adam_params* params, panna_stream_t stream);
+
+/* Freeze (frozen != 0) or release the weights and biases of layer `layer` (0 = first) of
+ * species `species` for panna_adam_step. */
+panna_status panna_set_frozen(panna_ctx* ctx, int32_t species, int32_t layer, int32_t frozen);
+
 /* Synchronise `stream` and return (and clear) the device status word. */
 panna_status panna_check(panna_ctx* ctx, panna_stream_t stream);
 

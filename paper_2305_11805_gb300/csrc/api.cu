@@ -82,6 +82,8 @@ struct panna_ctx {
     int force_variant[3] = {-1, -1, -1};   // descriptor, adjoint, jvp: -1 = tuned
     int fp32_tc = TF32_TAN | TF32_WGRAD;   // FP32 networks: first-layer products on the tensor cores
     int64_t norm_C = 0, norm_N = 0;   // loss normalisers (0 = the batch's own counts)
+    LossOpts loss_opts{0, 0, 0, 0.0, 0.0};
+    bool frozen[kMaxSpecies][kMaxLayers] = {};
     int last_launches = 0;
     // autotuner: kernel variant per problem signature, measured on the first call
     struct Tuned { int64_t N, C; int cap, prec; int variant[3]; };   // -1 = not measured yet
@@ -313,6 +315,34 @@ struct Request {
     const Work* cand = nullptr;  // dynamics: refresh these candidates instead of a neighbour search
 };
 
+// parameter ranges of the weights (biases excluded) of every layer of every species
+ParamRanges weight_ranges(const MlpPlan& p)
+{
+    ParamRanges r{};
+    for (int s = 0; s < p.S; ++s)
+        for (int l = 0; l < p.L; ++l) {
+            r.off[r.n] = p.w_off[s][l];
+            r.len[r.n] = (int64_t)p.widths[s][l + 1] * p.widths[s][l];
+            ++r.n;
+        }
+    return r;
+}
+
+// parameter ranges (weights and biases) of the frozen layers
+ParamRanges frozen_ranges(const panna_ctx* c)
+{
+    ParamRanges r{};
+    const MlpPlan& p = c->plan;
+    for (int s = 0; s < p.S; ++s)
+        for (int l = 0; l < p.L; ++l)
+            if (c->frozen[s][l]) {
+                r.off[r.n] = p.w_off[s][l];
+                r.len[r.n] = (int64_t)p.widths[s][l + 1] * (p.widths[s][l] + 1);
+                ++r.n;
+            }
+    return r;
+}
+
 // Kernel variants (0 blocked, 1 flattened) of the descriptor-family kernels for this problem
 // signature: measured once per kernel (each variant launched once to warm up, then timed
 // with CUDA events on the caller's stream), then cached.  Asynchronous calls never measure
@@ -424,7 +454,8 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         const double* alpha = nullptr;
         if (rq.train) {
             stage_mark(c, 7, s);
-            CU(launch_loss(L.w, c->norm_C, c->norm_N, E_cfg, rq.E_ref, F, rq.F_ref, rq.w_force, rq.loss,
+            CU(launch_loss(L.w, c->norm_C, c->norm_N, c->loss_opts, weight_ranges(c->plan), rq.theta, E_cfg,
+                           rq.E_ref, F, rq.F_ref, rq.w_force, rq.loss,
                            L.alpha_cfg, L.u, L.loss_part, s, &nl));
             u = L.u;
             alpha = L.alpha_cfg;
@@ -451,6 +482,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         const WgradTc wtc{(tf && (tfm & TF32_WGRAD)) ? L.tf_ws : nullptr, tfm, L.w.status};
         if (tan_tc) CU(tf32_tangent1(c->plan, L.mb, N, L.tf_ws, tfm, L.wdot, L.w.status, s, &nl));
         CU(mlp_param_grad(c->plan, L.mb, rq.theta, N, L.wdot, L.alpha_rows, rq.dtheta, s, &nl, tan_tc, &wtc));
+        if (rq.train) CU(launch_penalty_grad(c->loss_opts, weight_ranges(c->plan), rq.theta, rq.dtheta, s, &nl));
     }
     if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
     return PANNA_OK;
@@ -747,6 +779,43 @@ panna_status panna_md_run(panna_ctx* c, const panna_system* sys, double* vel, co
     }
     if (n_builds) *n_builds = builds;
     return collect(c, L, s, &need);
+}
+
+panna_status panna_set_loss_options(panna_ctx* c, const panna_loss_options* o)
+{
+    if (!c) return fail(PANNA_ERR_INVALID_ARG, "null context");
+    if (!o) { c->loss_opts = LossOpts{0, 0, 0, 0.0, 0.0}; return PANNA_OK; }
+    if (o->energy_loss < 0 || o->energy_loss > 1 || o->force_loss < 0 || o->force_loss > 1 ||
+        !(o->l1 >= 0.0) || !(o->l2 >= 0.0))
+        return fail(PANNA_ERR_INVALID_ARG, "loss kinds must be 0 or 1, penalties >= 0");
+    c->loss_opts = LossOpts{o->energy_loss, o->force_loss, o->energy_per_atom ? 1 : 0, o->l1, o->l2};
+    return PANNA_OK;
+}
+
+panna_status panna_set_frozen(panna_ctx* c, int32_t species, int32_t layer, int32_t frozen)
+{
+    if (!c) return fail(PANNA_ERR_INVALID_ARG, "null context");
+    if (species < 0 || species >= c->plan.S || layer < 0 || layer >= c->plan.L)
+        return fail(PANNA_ERR_INVALID_ARG, "species %d / layer %d out of range", species, layer);
+    c->frozen[species][layer] = frozen != 0;
+    return PANNA_OK;
+}
+
+panna_status panna_adam_step(panna_ctx* c, float* theta, const float* grad, float* m, float* v, int64_t t,
+                             const panna_adam_params* a, panna_stream_t stream)
+{
+    if (!c || !theta || !grad || !m || !v || !a) return fail(PANNA_ERR_INVALID_ARG, "null argument");
+    if (t < 1 || !(a->lr > 0.0) || !(a->beta1 >= 0.0 && a->beta1 < 1.0) || !(a->beta2 >= 0.0 && a->beta2 < 1.0) ||
+        !(a->eps >= 0.0) || !(a->decay_steps >= 0.0) || !(a->decay_rate > 0.0))
+        return fail(PANNA_ERR_INVALID_ARG, "Adam needs t >= 1, lr > 0, betas in [0, 1), eps >= 0, decay rate > 0");
+    CU(cudaSetDevice(c->device));
+    const double lr = a->decay_steps > 0.0 ? a->lr * pow(a->decay_rate, (double)t / a->decay_steps) : a->lr;
+    const double c1 = 1.0 - pow(a->beta1, (double)t), c2 = 1.0 - pow(a->beta2, (double)t);
+    int nl = 0;
+    CU(launch_adam(c->plan.P, theta, grad, m, v, lr, a->beta1, a->beta2, c1, c2, a->eps, frozen_ranges(c),
+                   (cudaStream_t)stream, &nl));
+    c->last_launches = nl;
+    return PANNA_OK;
 }
 
 panna_status panna_set_loss_normalization(panna_ctx* c, int64_t n_cfg_total, int64_t n_atoms_total)

@@ -132,11 +132,22 @@ cudaError_t launch_md_b(int64_t N, const int32_t* species, const MdSpecies& ms, 
 int cfg_chunks(int64_t N, int64_t C);
 cudaError_t launch_cfg_reduce(const Work& w, const float* E_rows, const float* vir_atom, double* E_cfg, double* virial,
                               float* E_atom, double* part, cudaStream_t s, int* launches);
-constexpr int kLossParts = 2 * 120;
+constexpr int kLossParts = 4 * 120;   // (energy, force) and (L1, L2) sums per block
+// Loss options (Sec. II.A): term kind 0 = x^2, 1 = exp(x^2) - 1 for energies and forces,
+// energies per configuration or per atom, L1/L2 penalty over the weights listed in `wr`
+struct LossOpts { int e_kind, f_kind, e_per_atom; double l1, l2; };
+struct ParamRanges { int n; int64_t off[kMaxSpecies * kMaxLayers]; int64_t len[kMaxSpecies * kMaxLayers]; };
 // C_norm, N_norm <= 0: normalise by the batch's own counts w.C, w.N
-cudaError_t launch_loss(const Work& w, int64_t C_norm, int64_t N_norm, const double* E_cfg, const double* E_ref,
-                        const float* F, const float* F_ref, double w_force, double* loss, double* alpha_cfg, float* u,
-                        double* part, cudaStream_t s, int* launches);
+cudaError_t launch_loss(const Work& w, int64_t C_norm, int64_t N_norm, const LossOpts& lo, const ParamRanges& wr,
+                        const float* theta, const double* E_cfg, const double* E_ref, const float* F,
+                        const float* F_ref, double w_force, double* loss, double* alpha_cfg, float* u, double* part,
+                        cudaStream_t s, int* launches);
+// dtheta += l1 sign(w) + 2 l2 w over the weights in wr
+cudaError_t launch_penalty_grad(const LossOpts& lo, const ParamRanges& wr, const float* theta, float* dtheta,
+                                cudaStream_t s, int* launches);
+// one fused Adam step over P parameters (entries inside `frozen` keep theta, m, v)
+cudaError_t launch_adam(int64_t P, float* theta, const float* g, float* m, float* v, double lr, double b1, double b2,
+                        double c1, double c2, double eps, const ParamRanges& frozen, cudaStream_t s, int* launches);
 cudaError_t launch_row_scale(const Work& w, const double* alpha_cfg, float* alpha_rows, cudaStream_t s, int* launches);
 
 // message returned by panna_last_error() on this thread (api.cu)

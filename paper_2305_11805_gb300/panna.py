@@ -51,6 +51,19 @@ class panna_md_params(C.Structure):
                 ("mass", C.POINTER(C.c_double)), ("seed", C.c_uint64), ("step0", C.c_int64)]
 
 
+class panna_loss_options(C.Structure):
+    _fields_ = [("energy_loss", C.c_int32), ("force_loss", C.c_int32), ("energy_per_atom", C.c_int32),
+                ("l1", C.c_double), ("l2", C.c_double)]
+
+
+class panna_adam_params(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("decay_rate", C.c_double), ("decay_steps", C.c_double)]
+
+
+PANNA_LOSS_QUADRATIC, PANNA_LOSS_EXPONENTIAL = 0, 1
+
+
 class PannaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("panna status %d: %s" % (status, msg))
@@ -84,6 +97,9 @@ def load(path: str = LIB_PATH):
         "panna_set_angular_precision": (i32, [_vp, i32]),
         "panna_set_tuning": (i32, [_vp, C.c_char_p, i32]),
         "panna_set_loss_normalization": (i32, [_vp, i64, i64]),
+        "panna_set_loss_options": (i32, [_vp, C.POINTER(panna_loss_options)]),
+        "panna_set_frozen": (i32, [_vp, i32, i32, i32]),
+        "panna_adam_step": (i32, [_vp, _vp, _vp, _vp, _vp, i64, C.POINTER(panna_adam_params), _vp]),
         "panna_md_run": (i32, [_vp, C.POINTER(panna_system), _vp, _vp, i32, C.POINTER(panna_md_params), i64, _vp,
                                i32, _vp, _vp, C.POINTER(i64), _vp]),
         "panna_neighbors": (i32, [_vp, C.POINTER(panna_system), i64, _vp, _vp, _vp, C.POINTER(i64), _vp]),
@@ -110,7 +126,7 @@ def exported_symbols() -> Sequence[str]:
     return ["panna_version", "panna_last_error", "panna_descriptor_size", "panna_create", "panna_destroy",
             "panna_param_count", "panna_set_neighbor_capacity", "panna_neighbor_capacity", "panna_set_async",
             "panna_check", "panna_set_angular_precision", "panna_set_tuning", "panna_set_loss_normalization",
-            "panna_md_run",
+            "panna_md_run", "panna_set_loss_options", "panna_set_frozen", "panna_adam_step",
             "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
             "panna_descriptors_static", "panna_capture", "panna_replay"]
@@ -211,6 +227,22 @@ def panna_md_run(ctx: int, sysd: "DeviceSystem", vel, theta, prec: int, dt: floa
                                _ptr(F), 1 if forces_valid else 0, _ptr(E_cfg), _ptr(E_traj), C.byref(nb),
                                _stream(stream)))
     return int(nb.value)
+
+
+def panna_set_loss_options(ctx: int, energy_loss=0, force_loss=0, energy_per_atom=False, l1=0.0, l2=0.0):
+    o = panna_loss_options(int(energy_loss), int(force_loss), 1 if energy_per_atom else 0, float(l1), float(l2))
+    _check(load().panna_set_loss_options(ctx, C.byref(o)))
+
+
+def panna_set_frozen(ctx: int, species: int, layer: int, frozen: bool):
+    _check(load().panna_set_frozen(ctx, int(species), int(layer), 1 if frozen else 0))
+
+
+def panna_adam_step(ctx: int, theta, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8,
+                    decay_rate=1.0, decay_steps=0.0, stream=None):
+    a = panna_adam_params(float(lr), float(beta1), float(beta2), float(eps), float(decay_rate), float(decay_steps))
+    _check(load().panna_adam_step(ctx, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), int(t), C.byref(a),
+                                  _stream(stream)))
 
 
 def panna_check(ctx: int, stream=None):
