@@ -193,6 +193,26 @@ def neighbor_list(system, rc: float):
         cap = int(n)
 
 
+def jacobians(system, desc):
+    """Per neighbour entry e = (i, j, n) of the sorted neighbour list, J[e] = dG_i/dr_e as a
+    [D, 3] array (Sec. II: the derivative the forces contract with dE_i/dG_i), from the
+    centre routine's Jacobian.  Returns dict(i, j, shift, r[P,3], J[P,D,3])."""
+    s = system
+    ii, jj, sh = neighbor_list(s, desc.rc)
+    D = descriptor_size(desc)
+    cfg = np.searchsorted(np.asarray(s.atom_off), ii, side="right") - 1
+    cells = np.asarray(s.cell, np.float64).reshape(-1, 3, 3)
+    r = np.asarray(s.pos)[jj] - np.asarray(s.pos)[ii] + np.einsum("pa,pab->pb", sh.astype(np.float64), cells[cfg])
+    J = np.zeros((len(ii), D, 3))
+    starts = np.searchsorted(ii, np.arange(s.n_atoms + 1))
+    for i in range(s.n_atoms):
+        a, b = starts[i], starts[i + 1]
+        if b > a:
+            _, Ji = center(desc, r[a:b], np.asarray(s.species)[jj[a:b]])
+            J[a:b] = Ji.transpose(1, 0, 2)
+    return dict(i=ii, j=jj, shift=sh, r=r, J=J)
+
+
 def batch(system, desc, archs, theta, want_G: bool = False, e_ref=None, f_ref=None,
           w_force: float = 0.1, param_grad: bool = False, ghost=None, norm=None, loss_options=None):
     """Whole-batch FP64 evaluation; returns a dict of numpy arrays (see orc_batch).
