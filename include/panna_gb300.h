@@ -378,6 +378,86 @@ panna_status panna_loss_grad(panna_ctx* ctx, const panna_system* sys, const floa
                              panna_stream_t stream);
 
 /*
+ * Precomputed descriptors with stored Jacobians (Sec. II.A: descriptors can be computed
+ * once for a whole dataset and reused in every epoch, with their derivatives stored for the
+ * forces, at the price of the memory that takes; the default path recomputes them in every
+ * call).  A store holds one batch; on a GPU with 288 GB of HBM a dataset of many batches can
+ * stay resident, and a training step then streams the stored Jacobians instead of
+ * recomputing the angular terms.
+ *
+ * Use: panna_store_plan (neighbour search, sizes) -> allocate info.bytes of device memory,
+ * 256-byte aligned -> panna_store_build -> any number of panna_store_energy_forces /
+ * panna_store_loss_grad calls with that batch's panna_system (only n_cfg, n_atoms and
+ * atom_off are read; the other pointers may be NULL) and any parameters theta.
+ *
+ * Binary format of a store (a documented layout, so that descriptors and derivatives made
+ * by other programs can be used): nine sections, each starting at the next multiple of 256
+ * bytes from the buffer start (panna_store_sections returns the byte offsets), in order:
+ *   0 G           float32 [n_atoms][D]     descriptor rows in network order: rows of species s
+ *                                          are seg_off[s]..seg_off[s+1]-1, row r is atom
+ *                                          atom_of_row[r]
+ *   1 row_of_atom int32   [n_atoms]
+ *   2 atom_of_row int32   [n_atoms]
+ *   3 seg_off     int32   [S+1]
+ *   4 atom_cfg    int32   [n_atoms]        configuration of each atom
+ *   5 ent_off     int64   [n_atoms+1]      neighbour entries of atom i: ent_off[i]..ent_off[i+1]-1
+ *   6 ent_idx     int32   [n_entries][2]   (j, species of j) of entry e = (i, j, n)
+ *   7 ent_vec     float32 [n_entries][4]   (r_e = x_j + n.cell - x_i, |r_e|)
+ *   8 jac         float32 [n_entries][3][width]: jac[e][a][c] = d G_i[col(c)] / d r_e[a], where
+ *                 with Rp = 4 ceil(n_rad/4), A = n_theta n_ang_r, Ap = 4 ceil(A/4),
+ *                 width = Rp + S Ap, s_j the neighbour's species:
+ *                   c < Rp:              col = s_j n_rad + c                   (c < n_rad)
+ *                   c = Rp + s Ap + l:   col = S n_rad + blk(min(s_j,s), max(s_j,s)) A + l  (l < A)
+ *                 blk(a, b) the upper-triangle block index of the descriptor layout; the
+ *                 padding columns (c >= n_rad below Rp, l >= A) hold zeros.  All other
+ *                 columns of dG_i/dr_e are zero by the descriptor's definition.
+ * The library's build evaluates J in FP64 and rounds it to FP32; G is the FP32 descriptor of
+ * panna_descriptors.  Stores take batches without ghost atoms, D <= 49152 and at most 2048
+ * neighbours per atom (PANNA_ERR_UNSUPPORTED otherwise).  The evaluation calls check the
+ * sizes of a store but not its contents: a store written by another program must hold
+ * indices in range (j < n_atoms, species < S, offsets within the sections).
+ */
+typedef struct {
+    int64_t n_atoms;     /* batch the store was planned for */
+    int64_t n_cfg;
+    int64_t n_entries;   /* neighbour entries (i, j, n) */
+    int32_t D;           /* descriptor size */
+    int32_t width;       /* Jacobian columns per entry and Cartesian component */
+    int64_t bytes;       /* device bytes of the store */
+} panna_store_info;
+
+/* Neighbour search of `sys` and the store's sizes into *info (host).  Synchronous. */
+panna_status panna_store_plan(panna_ctx* ctx, const panna_system* sys, panna_store_info* info,
+                              panna_stream_t stream);
+
+/* Byte offsets of the nine sections above for a planned store: offsets[9] (host). */
+panna_status panna_store_sections(const panna_ctx* ctx, const panna_store_info* info, int64_t* offsets);
+
+/*
+ * Fill `store` (device, info->bytes, 256-byte aligned, caller-owned) for the batch `sys` that
+ * was planned (its positions must give the same number of neighbour entries, else
+ * PANNA_ERR_INVALID_ARG).  Synchronous.
+ */
+panna_status panna_store_build(panna_ctx* ctx, const panna_system* sys, const panna_store_info* info,
+                               void* store, panna_stream_t stream);
+
+/* panna_energy_forces from a store (same outputs, same precisions). */
+panna_status panna_store_energy_forces(panna_ctx* ctx, const panna_system* sys, const panna_store_info* info,
+                                       const void* store, const float* theta, int32_t mlp_precision,
+                                       double* E_cfg, float* E_atom, float* F, double* virial,
+                                       panna_stream_t stream);
+
+/*
+ * panna_loss_grad from a store (same loss, options, normalisers and outputs).  The force
+ * part of the gradient takes the descriptor tangent w_i = sum_e J_e (u_j(e) - u_i) from the
+ * stored Jacobians.
+ */
+panna_status panna_store_loss_grad(panna_ctx* ctx, const panna_system* sys, const panna_store_info* info,
+                                   const void* store, const float* theta, const double* E_ref,
+                                   const float* F_ref, double w_force, double* loss, float* dtheta,
+                                   double* E_cfg, float* F, panna_stream_t stream);
+
+/*
  * CUDA-graph form of panna_energy_forces for repeated evaluation of one ragged batch (the
  * same device arrays, contents updated in place, e.g. positions in an MD loop):
  * panna_capture runs the call once synchronously (sizing the workspace, tuning kernel

@@ -85,6 +85,7 @@ struct panna_ctx {
     LossOpts loss_opts{0, 0, 0, 0.0, 0.0};
     bool frozen[kMaxSpecies][kMaxLayers] = {};
     int last_launches = 0;
+    DescGrid64 g64{};                 // FP64 descriptor parameters (stored Jacobians)
     // autotuner: kernel variant per problem signature, measured on the first call
     struct Tuned { int64_t N, C; int cap, prec; int variant[3]; };   // -1 = not measured yet
     Tuned tuned[16];
@@ -243,12 +244,14 @@ panna_status prepare(panna_ctx* c, const panna_system* sys, bool train, bool bf1
     return PANNA_OK;
 }
 
-panna_status check_system(const panna_ctx* c, const panna_system* sys)
+// geometry = false: a batch evaluated from stored descriptors (only the counts and atom_off)
+panna_status check_system(const panna_ctx* c, const panna_system* sys, bool geometry = true)
 {
     if (!c || !sys) return fail(PANNA_ERR_INVALID_ARG, "null context or system");
     if (sys->n_cfg < 1 || sys->n_atoms < 0) return fail(PANNA_ERR_INVALID_ARG, "n_cfg must be >= 1, n_atoms >= 0");
     if (sys->n_atoms > ((int64_t)1 << 31) - 1) return fail(PANNA_ERR_UNSUPPORTED, "more than 2^31-1 atoms");
-    if (!sys->atom_off || !sys->cell || !sys->pbc || (sys->n_atoms > 0 && (!sys->pos || !sys->species)))
+    if (!sys->atom_off) return fail(PANNA_ERR_INVALID_ARG, "null atom_off");
+    if (geometry && (!sys->cell || !sys->pbc || (sys->n_atoms > 0 && (!sys->pos || !sys->species))))
         return fail(PANNA_ERR_INVALID_ARG, "null system array");
     return PANNA_OK;
 }
@@ -313,6 +316,7 @@ struct Request {
     const float* dF = nullptr;
     float* dtheta = nullptr;
     const Work* cand = nullptr;  // dynamics: refresh these candidates instead of a neighbour search
+    const StoreView* store = nullptr;   // stored descriptors and Jacobians instead of geometry
 };
 
 // parameter ranges of the weights (biases excluded) of every layer of every species
@@ -390,19 +394,30 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
     c->n_marked = 0;
     CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
-    stage_mark(c, 0, s);
-    if (rq.cand) CU(refresh_neighbors(*rq.cand, L.w, c->d, s, &nl));
-    else CU(build_neighbors(L.w, c->d, s, &nl));
-    if (rq.G_out) {
+    const StoreView* sv = rq.store;
+    if (sv) {
+        // stored descriptors: rows, maps and configuration indices come from the store
+        L.w.row_of_atom = sv->row_of_atom;
+        L.w.atom_of_row = sv->atom_of_row;
+        L.w.seg_off = sv->seg_off;
+        L.w.atom_cfg = sv->atom_cfg;
+        L.G = sv->G;
+        L.mb.G = sv->G;
+        L.mb.seg_off = sv->seg_off;
+        CU(mlp_tiles(c->plan, L.w.seg_off, L.mb.tile_start, s, &nl));
+    } else {
+        stage_mark(c, 0, s);
+        if (rq.cand) CU(refresh_neighbors(*rq.cand, L.w, c->d, s, &nl));
+        else CU(build_neighbors(L.w, c->d, s, &nl));
+        if (rq.G_out) {
+            stage_mark(c, 1, s);
+            CU(launch_descriptor(L.w, c->d, rq.G_out, nullptr, c->ang_mode != 2, s, &nl));
+            if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
+            return PANNA_OK;
+        }
+        CU(species_order(L.w, c->d.S, s, &nl));
+        CU(mlp_tiles(c->plan, L.w.seg_off, L.mb.tile_start, s, &nl));
         stage_mark(c, 1, s);
-        CU(launch_descriptor(L.w, c->d, rq.G_out, nullptr, c->ang_mode != 2, s, &nl));
-        if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
-        return PANNA_OK;
-    }
-    CU(species_order(L.w, c->d.S, s, &nl));
-    CU(mlp_tiles(c->plan, L.w.seg_off, L.mb.tile_start, s, &nl));
-    stage_mark(c, 1, s);
-    {
         int dummy = 0;
         const int v = tuned_variant(c, sys, rq.prec, KV_DESC, s, [&](int vv) {
             launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &dummy, vv);
@@ -439,12 +454,17 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
             CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl));
         }
         stage_mark(c, 3, s);
-        int dummy = 0;
-        const int variant = tuned_variant(c, sys, rq.prec, KV_ADJ, s, [&](int vv) {
-            launch_adjoint(L.w, c->d, L.g, L.F_tune, nullptr, acc, vv, s, &dummy);
-        });
-        CU(cudaMemsetAsync(F, 0, sizeof(float) * 3 * N, s));
-        CU(launch_adjoint(L.w, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, acc, variant, s, &nl));
+        if (sv) {
+            CU(cudaMemsetAsync(F, 0, sizeof(float) * 3 * N, s));
+            CU(launch_store_adjoint(*sv, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, s, &nl));
+        } else {
+            int dummy = 0;
+            const int variant = tuned_variant(c, sys, rq.prec, KV_ADJ, s, [&](int vv) {
+                launch_adjoint(L.w, c->d, L.g, L.F_tune, nullptr, acc, vv, s, &dummy);
+            });
+            CU(cudaMemsetAsync(F, 0, sizeof(float) * 3 * N, s));
+            CU(launch_adjoint(L.w, c->d, L.g, F, rq.virial ? L.vir_atom : nullptr, acc, variant, s, &nl));
+        }
     }
     stage_mark(c, 4, s);
     CU(launch_cfg_reduce(L.w, L.E_rows, (rq.virial && need_forces) ? L.vir_atom : nullptr, E_cfg, rq.virial,
@@ -465,7 +485,9 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         }
         CU(launch_row_scale(L.w, alpha, L.alpha_rows, s, &nl));
         stage_mark(c, 5, s);
-        if (u) {
+        if (u && sv) {
+            CU(launch_store_tangent(*sv, c->d, u, L.wdot, s, &nl));
+        } else if (u) {
             // the tangent enters only the weight gradient (tolerance 1e-4 against 1e-5 for
             // forces): the plain FP32 angular form unless extended precision is forced
             const bool acc_jvp = c->ang_mode == 1;
@@ -490,7 +512,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
 
 panna_status run(panna_ctx* c, const panna_system* sys, const Request& rq, cudaStream_t s)
 {
-    ST(check_system(c, sys));
+    ST(check_system(c, sys, rq.store == nullptr));
     CU(cudaSetDevice(c->device));
     const bool train = rq.train || rq.vjp;
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -598,6 +620,15 @@ panna_status panna_create(const panna_desc_params* p, int32_t n_archs, const pan
         c->d.half_sin_lo[k] = (float)(hs - (double)(float)hs);
     }
     c->d.eps_theta_lo = (float)(p->eps_theta - (double)(float)p->eps_theta);
+    DescGrid64& g64 = c->g64;
+    g64.rc = p->rc; g64.eta_rad = p->eta_rad; g64.eta_ang = p->eta_ang; g64.zeta = p->zeta;
+    g64.eps_theta = p->eps_theta; g64.pref = pow(2.0, 1.0 - p->zeta); g64.zeta_int = d.zeta_int;
+    for (int k = 0; k < p->n_rad; ++k) g64.rs_rad[k] = p->rs_rad[k];
+    for (int k = 0; k < p->n_ang_r; ++k) g64.rs_ang[k] = p->rs_ang[k];
+    for (int k = 0; k < p->n_theta; ++k) {
+        g64.cos_t[k] = cos(p->theta_s[k]);
+        g64.sin_t[k] = sin(p->theta_s[k]);
+    }
     MlpPlan& pl = c->plan;
     pl.S = d.S;
     pl.L = archs[0].n_layers;
@@ -922,6 +953,160 @@ panna_status panna_loss_grad(panna_ctx* c, const panna_system* sys, const float*
     Request rq;
     rq.theta = theta; rq.train = true; rq.E_ref = E_ref; rq.F_ref = F_ref; rq.w_force = w_force; rq.loss = loss;
     rq.dtheta = dtheta; rq.E_cfg = E_cfg; rq.F = F; rq.forces = true; rq.energy = true;
+    return run(c, sys, rq, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ stored descriptors
+
+static panna_status store_view(const panna_ctx* c, const panna_system* sys, const panna_store_info* info,
+                               const void* store, StoreView& v)
+{
+    if (!info || !store) return fail(PANNA_ERR_INVALID_ARG, "null store info or buffer");
+    if ((uintptr_t)store % 256 != 0) return fail(PANNA_ERR_INVALID_ARG, "the store buffer must be 256-byte aligned");
+    if (info->n_atoms != sys->n_atoms || info->n_cfg != sys->n_cfg)
+        return fail(PANNA_ERR_INVALID_ARG, "store of another batch (%lld atoms, %lld configurations)",
+                    (long long)info->n_atoms, (long long)info->n_cfg);
+    v = StoreView{};
+    v.N = info->n_atoms;
+    v.C = info->n_cfg;
+    v.P = info->n_entries;
+    store_dims(c->d, v);
+    if (info->D != v.D || info->width != v.W || v.P < 0)
+        return fail(PANNA_ERR_INVALID_ARG, "store of another descriptor (D %d, width %d)", info->D, info->width);
+    if (store_carve(v, reinterpret_cast<char*>(const_cast<void*>(store)), nullptr) != info->bytes)
+        return fail(PANNA_ERR_INVALID_ARG, "store size does not match its entry count");
+    return PANNA_OK;
+}
+
+// neighbour search of a batch for a store; *total (host) = number of entries (synchronous)
+static panna_status store_search(panna_ctx* c, const panna_system* sys, Layout& L, int64_t* total, cudaStream_t s)
+{
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        ST(prepare(c, sys, false, false, L, s));
+        c->last_launches = 0;
+        CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
+        CU(build_neighbors(L.w, c->d, s, &c->last_launches));
+        CU(launch_store_offsets(L.w, L.w.cell_start, s, &c->last_launches));
+        CU(cudaMemcpyAsync(total, L.w.cell_start + sys->n_atoms, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        int need = 0;
+        panna_status st = collect(c, L, s, &need);   // synchronises the stream
+        if (st == PANNA_ERR_NEIGHBOR_OVERFLOW && attempt == 0) {
+            c->cap = need + need / 4 + 8;
+            continue;
+        }
+        if (st != PANNA_OK) return st;
+        if (c->cap > kStoreMaxCap)
+            return fail(PANNA_ERR_UNSUPPORTED, "stored Jacobians take at most %d neighbours per atom", kStoreMaxCap);
+        return PANNA_OK;
+    }
+    return PANNA_OK;
+}
+
+panna_status panna_store_plan(panna_ctx* c, const panna_system* sys, panna_store_info* info, panna_stream_t stream)
+{
+    ST(check_system(c, sys));
+    if (!info) return fail(PANNA_ERR_INVALID_ARG, "null info");
+    if (sys->ghost) return fail(PANNA_ERR_UNSUPPORTED, "stored descriptors of a batch with ghost atoms");
+    if (c->d.D > kStoreMaxD) return fail(PANNA_ERR_UNSUPPORTED, "stored descriptors take D <= %d", kStoreMaxD);
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(c->device));
+    Layout L;
+    int64_t n_entries = 0;
+    ST(store_search(c, sys, L, &n_entries, s));
+    StoreView v{};
+    v.N = sys->n_atoms;
+    v.C = sys->n_cfg;
+    v.P = n_entries;
+    store_dims(c->d, v);
+    info->n_atoms = v.N;
+    info->n_cfg = v.C;
+    info->n_entries = v.P;
+    info->D = v.D;
+    info->width = v.W;
+    info->bytes = store_carve(v, nullptr, nullptr);
+    return PANNA_OK;
+}
+
+panna_status panna_store_sections(const panna_ctx* c, const panna_store_info* info, int64_t* offsets)
+{
+    if (!c || !info || !offsets) return fail(PANNA_ERR_INVALID_ARG, "null argument");
+    StoreView v{};
+    v.N = info->n_atoms;
+    v.C = info->n_cfg;
+    v.P = info->n_entries;
+    store_dims(c->d, v);
+    store_carve(v, nullptr, offsets);
+    return PANNA_OK;
+}
+
+panna_status panna_store_build(panna_ctx* c, const panna_system* sys, const panna_store_info* info, void* store,
+                               panna_stream_t stream)
+{
+    ST(check_system(c, sys));
+    if (sys->ghost) return fail(PANNA_ERR_UNSUPPORTED, "stored descriptors of a batch with ghost atoms");
+    StoreView v;
+    ST(store_view(c, sys, info, store, v));
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(c->device));
+    Layout L;
+    int64_t total = 0;
+    ST(store_search(c, sys, L, &total, s));
+    if (total != v.P)
+        return fail(PANNA_ERR_INVALID_ARG, "the batch has %lld neighbour entries, the store was planned for %lld",
+                    (long long)total, (long long)v.P);
+    int& nl = c->last_launches;
+    CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
+    CU(species_order(L.w, c->d.S, s, &nl));
+    CU(launch_store_offsets(L.w, v.ent_off, s, &nl));
+    const bool acc = c->ang_mode != 2;
+    int dummy = 0;
+    const int variant = tuned_variant(c, sys, PANNA_MLP_FP32, KV_DESC, s, [&](int vv) {
+        launch_descriptor(L.w, c->d, v.G, L.w.row_of_atom, acc, s, &dummy, vv);
+    });
+    CU(launch_descriptor(L.w, c->d, v.G, L.w.row_of_atom, acc, s, &nl, variant));
+    const int64_t N = sys->n_atoms;
+    CU(cudaMemcpyAsync(v.row_of_atom, L.w.row_of_atom, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(v.atom_of_row, L.w.atom_of_row, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(v.seg_off, L.w.seg_off, sizeof(int32_t) * (c->d.S + 1), cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(v.atom_cfg, L.w.atom_cfg, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));
+    CU(launch_store_entries(L.w, v, s, &nl));
+    CU(launch_store_jacobian(L.w, c->d, c->g64, v, s, &nl));
+    CU(cudaGetLastError());
+    int need = 0;
+    return collect(c, L, s, &need);
+}
+
+panna_status panna_store_energy_forces(panna_ctx* c, const panna_system* sys, const panna_store_info* info,
+                                       const void* store, const float* theta, int32_t prec, double* E_cfg,
+                                       float* E_atom, float* F, double* virial, panna_stream_t stream)
+{
+    ST(check_system(c, sys, false));
+    if (!theta || !E_cfg || !F) return fail(PANNA_ERR_INVALID_ARG, "theta, E_cfg and F are required");
+    if (prec != PANNA_MLP_FP32 && prec != PANNA_MLP_BF16 && prec != PANNA_MLP_BF16_FAST)
+        return fail(PANNA_ERR_INVALID_ARG, "bad precision");
+    if (prec != PANNA_MLP_FP32 && (c->plan.L < 2 || c->d.D % 8 != 0))
+        return fail(PANNA_ERR_UNSUPPORTED, "BF16 networks need a hidden layer and D a multiple of 8");
+    StoreView v;
+    ST(store_view(c, sys, info, store, v));
+    Request rq;
+    rq.theta = theta; rq.prec = prec; rq.E_cfg = E_cfg; rq.E_atom = E_atom; rq.F = F; rq.virial = virial;
+    rq.forces = true; rq.energy = true; rq.store = &v;
+    return run(c, sys, rq, (cudaStream_t)stream);
+}
+
+panna_status panna_store_loss_grad(panna_ctx* c, const panna_system* sys, const panna_store_info* info,
+                                   const void* store, const float* theta, const double* E_ref, const float* F_ref,
+                                   double w_force, double* loss, float* dtheta, double* E_cfg, float* F,
+                                   panna_stream_t stream)
+{
+    ST(check_system(c, sys, false));
+    if (!theta || !E_ref || !F_ref || !loss || !dtheta)
+        return fail(PANNA_ERR_INVALID_ARG, "theta, E_ref, F_ref, loss and dtheta are required");
+    StoreView v;
+    ST(store_view(c, sys, info, store, v));
+    Request rq;
+    rq.theta = theta; rq.train = true; rq.E_ref = E_ref; rq.F_ref = F_ref; rq.w_force = w_force; rq.loss = loss;
+    rq.dtheta = dtheta; rq.E_cfg = E_cfg; rq.F = F; rq.forces = true; rq.energy = true; rq.store = &v;
     return run(c, sys, rq, (cudaStream_t)stream);
 }
 

@@ -119,6 +119,48 @@ cudaError_t launch_adjoint(const Work& w, const DescDev& d, const float* g_rows,
 cudaError_t launch_jvp(const Work& w, const DescDev& d, const float* u, float* wdot_rows, bool acc, cudaStream_t s,
                        int* launches, int variant = 0);
 
+// FP64 copies of the descriptor parameters (the stored Jacobians are evaluated in FP64)
+struct DescGrid64 {
+    double rc, eta_rad, eta_ang, zeta, eps_theta, pref;   // pref = 2^(1 - zeta)
+    int32_t zeta_int;
+    double rs_rad[kMaxRad];
+    double rs_ang[kMaxAngR];
+    double cos_t[kMaxTheta], sin_t[kMaxTheta];
+};
+
+// Stored descriptors and Jacobians of one batch (store.cu): sections of one device buffer,
+// in the order and with the alignment that store_carve fixes.
+constexpr int kStoreSections = 9;
+struct StoreView {
+    int64_t N, C, P;            // atoms, configurations, neighbour entries
+    int32_t S, D, Rp, Ap, W;    // species, descriptor size, padded radial / block widths, columns
+    float* G;                   // [N][D] network-order rows
+    int32_t* row_of_atom;       // [N]
+    int32_t* atom_of_row;       // [N]
+    int32_t* seg_off;           // [S+1]
+    int32_t* atom_cfg;          // [N]
+    int64_t* ent_off;           // [N+1]
+    int2* ent_idx;              // [P] (j, species of j)
+    float4* ent_vec;            // [P] (r_e, |r_e|)
+    float* jac;                 // [P][3][W]
+};
+// widths from the descriptor; section offsets (bytes) into off[kStoreSections] when off is
+// non-null; pointers into `base` when it is non-null; returns the total size in bytes
+void store_dims(const DescDev& d, StoreView& v);
+int64_t store_carve(StoreView& v, char* base, int64_t* off);
+// off[0..N]: exclusive scan of the neighbour counts (entry offsets of each atom)
+cudaError_t launch_store_offsets(const Work& w, int64_t* off, cudaStream_t s, int* launches);
+cudaError_t launch_store_entries(const Work& w, const StoreView& v, cudaStream_t s, int* launches);
+cudaError_t launch_store_jacobian(const Work& w, const DescDev& d, const DescGrid64& g, const StoreView& v,
+                                  cudaStream_t s, int* launches);
+cudaError_t launch_store_adjoint(const StoreView& v, const DescDev& d, const float* g_rows, float* F, float* vir_atom,
+                                 cudaStream_t s, int* launches);
+cudaError_t launch_store_tangent(const StoreView& v, const DescDev& d, const float* u, float* wdot_rows,
+                                 cudaStream_t s, int* launches);
+// largest neighbour capacity and descriptor size the store kernels take
+constexpr int kStoreMaxCap = 2048;
+constexpr int kStoreMaxD = 49152;
+
 // Langevin dynamics (md.cu): per species a = (eV/A)/m in A/fs^2 and the thermal velocity
 // scale sigma = sqrt(kB T a) in A/fs
 struct MdSpecies { double acc[kMaxSpecies]; double sigma[kMaxSpecies]; };

@@ -64,6 +64,14 @@ class panna_adam_params(C.Structure):
 PANNA_LOSS_QUADRATIC, PANNA_LOSS_EXPONENTIAL = 0, 1
 
 
+class panna_store_info(C.Structure):
+    _fields_ = [("n_atoms", C.c_int64), ("n_cfg", C.c_int64), ("n_entries", C.c_int64), ("D", C.c_int32),
+                ("width", C.c_int32), ("bytes", C.c_int64)]
+
+
+STORE_SECTIONS = ("G", "row_of_atom", "atom_of_row", "seg_off", "atom_cfg", "ent_off", "ent_idx", "ent_vec", "jac")
+
+
 class PannaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("panna status %d: %s" % (status, msg))
@@ -113,6 +121,13 @@ def load(path: str = LIB_PATH):
         "panna_descriptors_static": (i32, [C.POINTER(panna_desc_params), C.POINTER(panna_system), _vp, _vp]),
         "panna_capture": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
         "panna_replay": (i32, [_vp, _vp]),
+        "panna_store_plan": (i32, [_vp, C.POINTER(panna_system), C.POINTER(panna_store_info), _vp]),
+        "panna_store_sections": (i32, [_vp, C.POINTER(panna_store_info), C.POINTER(i64)]),
+        "panna_store_build": (i32, [_vp, C.POINTER(panna_system), C.POINTER(panna_store_info), _vp, _vp]),
+        "panna_store_energy_forces": (i32, [_vp, C.POINTER(panna_system), C.POINTER(panna_store_info), _vp, _vp,
+                                            i32, _vp, _vp, _vp, _vp, _vp]),
+        "panna_store_loss_grad": (i32, [_vp, C.POINTER(panna_system), C.POINTER(panna_store_info), _vp, _vp, _vp,
+                                        _vp, f64, _vp, _vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -129,7 +144,8 @@ def exported_symbols() -> Sequence[str]:
             "panna_md_run", "panna_set_loss_options", "panna_set_frozen", "panna_adam_step",
             "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
-            "panna_descriptors_static", "panna_capture", "panna_replay"]
+            "panna_descriptors_static", "panna_capture", "panna_replay", "panna_store_plan",
+            "panna_store_sections", "panna_store_build", "panna_store_energy_forces", "panna_store_loss_grad"]
 
 
 def _check(status: int):
@@ -303,6 +319,36 @@ def panna_replay(ctx: int, stream=None):
     _check(load().panna_replay(ctx, _stream(stream)))
 
 
+def panna_store_plan(ctx: int, sysd: "DeviceSystem", stream=None) -> panna_store_info:
+    info = panna_store_info()
+    _check(load().panna_store_plan(ctx, C.byref(sysd.s), C.byref(info), _stream(stream)))
+    return info
+
+
+def panna_store_sections(ctx: int, info: panna_store_info):
+    off = (C.c_int64 * 9)()
+    _check(load().panna_store_sections(ctx, C.byref(info), off))
+    return [int(x) for x in off]
+
+
+def panna_store_build(ctx: int, sysd: "DeviceSystem", info: panna_store_info, store, stream=None):
+    _check(load().panna_store_build(ctx, C.byref(sysd.s), C.byref(info), _ptr(store), _stream(stream)))
+
+
+def panna_store_energy_forces(ctx: int, sysd: "DeviceSystem", info: panna_store_info, store, theta, prec: int,
+                              E_cfg, E_atom, F, virial, stream=None):
+    _check(load().panna_store_energy_forces(ctx, C.byref(sysd.s), C.byref(info), _ptr(store), _ptr(theta),
+                                            int(prec), _ptr(E_cfg), _ptr(E_atom), _ptr(F), _ptr(virial),
+                                            _stream(stream)))
+
+
+def panna_store_loss_grad(ctx: int, sysd: "DeviceSystem", info: panna_store_info, store, theta, E_ref, F_ref,
+                          w_force: float, loss, dtheta, E_cfg=None, F=None, stream=None):
+    _check(load().panna_store_loss_grad(ctx, C.byref(sysd.s), C.byref(info), _ptr(store), _ptr(theta),
+                                        _ptr(E_ref), _ptr(F_ref), float(w_force), _ptr(loss), _ptr(dtheta),
+                                        _ptr(E_cfg), _ptr(F), _stream(stream)))
+
+
 def panna_version() -> str:
     return load().panna_version().decode()
 
@@ -404,4 +450,56 @@ class Potential:
         E = torch.empty(sysd.n_cfg, dtype=torch.float64, device="cuda")
         F = torch.empty((sysd.n_atoms, 3), dtype=torch.float32, device="cuda")
         panna_loss_grad(self.ctx, sysd, theta, E_ref, F_ref, w_force, loss, g, E, F)
+        return loss, g, E, F
+
+
+class Store:
+    """Precomputed descriptors and Jacobians of one batch in a torch-owned device buffer
+    (the nine sections of the store format, at the offsets the library reports)."""
+
+    def __init__(self, pot: "Potential", sysd: DeviceSystem):
+        import torch
+        self.pot = pot
+        self.info = panna_store_plan(pot.ctx, sysd)
+        # torch's caching allocator returns blocks aligned to at least 512 bytes
+        self.buf = torch.empty(max(int(self.info.bytes), 1), dtype=torch.uint8, device="cuda")
+        if self.buf.data_ptr() % 256:
+            raise RuntimeError("store buffer is not 256-byte aligned")
+        panna_store_build(pot.ctx, sysd, self.info, self.buf)
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.info.bytes)
+
+    def sections(self):
+        """Views of the nine sections as torch tensors (shapes of the store format)."""
+        import torch
+        off = panna_store_sections(self.pot.ctx, self.info)
+        N, P, D, W = int(self.info.n_atoms), int(self.info.n_entries), int(self.info.D), int(self.info.width)
+        S = len(self.pot.archs)
+        spec = [(torch.float32, (N, D)), (torch.int32, (N,)), (torch.int32, (N,)), (torch.int32, (S + 1,)),
+                (torch.int32, (N,)), (torch.int64, (N + 1,)), (torch.int32, (P, 2)), (torch.float32, (P, 4)),
+                (torch.float32, (P, 3, W))]
+        out = {}
+        for name, o, (dt, shape) in zip(STORE_SECTIONS, off, spec):
+            n = int(np.prod(shape)) * torch.empty(0, dtype=dt).element_size()
+            out[name] = self.buf[o:o + n].view(dt).view(shape)
+        return out
+
+    def energy_forces(self, sysd: DeviceSystem, theta, prec: int = PANNA_MLP_FP32, virial: bool = True):
+        import torch
+        E = torch.empty(sysd.n_cfg, dtype=torch.float64, device="cuda")
+        Ea = torch.empty(sysd.n_atoms, dtype=torch.float32, device="cuda")
+        F = torch.empty((sysd.n_atoms, 3), dtype=torch.float32, device="cuda")
+        V = torch.empty((sysd.n_cfg, 3, 3), dtype=torch.float64, device="cuda") if virial else None
+        panna_store_energy_forces(self.pot.ctx, sysd, self.info, self.buf, theta, prec, E, Ea, F, V)
+        return E, Ea, F, V
+
+    def loss_grad(self, sysd: DeviceSystem, theta, E_ref, F_ref, w_force: float):
+        import torch
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty(self.pot.P, dtype=torch.float32, device="cuda")
+        E = torch.empty(sysd.n_cfg, dtype=torch.float64, device="cuda")
+        F = torch.empty((sysd.n_atoms, 3), dtype=torch.float32, device="cuda")
+        panna_store_loss_grad(self.pot.ctx, sysd, self.info, self.buf, theta, E_ref, F_ref, w_force, loss, g, E, F)
         return loss, g, E, F
