@@ -55,12 +55,15 @@ def dist_env():
 TRAFFIC_FILE = "profiles/geometry_kernels_molecules1024.md"
 
 
-def measured_traffic(kernel):
+STORE_TRAFFIC_FILE = "profiles/store_kernels_molecules1024.md"
+
+
+def measured_traffic(kernel, path=TRAFFIC_FILE):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when there is
     none or the kernel source has changed since the counters were taken."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, TRAFFIC_FILE)) as f:
+        with open(os.path.join(ROOT, path)) as f:
             line = [l for l in f if l.startswith("traffic_bytes_per_launch")][0]
     except (OSError, IndexError):
         return None
@@ -539,6 +542,7 @@ def run_stored(args):
               "jvp": jac_bytes + P_e * 8 + N * 12 + P_e * 12 + N * D * 4}
     dom = max(("adjoint", "jvp"), key=lambda k: stage.get(k, 0.0))
     ach = bytes_[dom] / (stage[dom] * 1e-3) / 1e9
+    traffic = measured_traffic(dom, STORE_TRAFFIC_FILE)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
@@ -548,7 +552,8 @@ def run_stored(args):
                       "on_the_fly_ms_per_step": otf_ms, "l2": "flushed between steps (256 MiB write)",
                       "stage_ms_per_step": {k: round(v, 4) for k, v in stage.items()}},
            "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                        "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
+                        "traffic_source": STORE_TRAFFIC_FILE if traffic is not None else None,
                         "peak_source": "%s hbm_gbs" % peak_kind, "algorithmic_bytes_per_launch": bytes_[dom],
                         "ms_per_launch": stage[dom]},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h_er.numel() * 8 + h_fr.numel() * 4,

@@ -371,12 +371,273 @@ k_store_adjoint(StoreView v, DescDev d, const float* __restrict__ g_rows, float*
     }
 }
 
+// Balanced variants.  The grid holds as many warps as fit on the GPU at once; warp w of T
+// takes the atoms whose entries fall in the w-th of T equal slices of all entries (whole
+// atoms, so no atom is split), which evens out molecules of 5 and of 30 atoms and leaves no
+// tail wave.  NP = passes of 32 float4 columns per entry row (W <= 128 NP): each lane decodes
+// its NP column positions once, then issues all 3 NP of its loads of an entry row before any
+// arithmetic, keeping about 4.6 kB per warp in flight for NP = 3.
+
+// first atom of warp w's range: the smallest i with ent_off[i] >= ceil(w P / T); N for w = T
+__device__ __forceinline__ int64_t range_start(const StoreView& v, int64_t w, int64_t T)
+{
+    if (w >= T) return v.N;
+    const int64_t target = (w * v.P + T - 1) / T;
+    int64_t lo = 0, hi = v.N;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (v.ent_off[mid] >= target) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// per lane and pass: neighbour-species-independent part of the column map
+template <int NP>
+struct LaneCols {
+    int loc[NP];     // radial column, or position inside an angular block
+    int spc[NP];     // -1: radial block; else the second species s of block {s_j, s}
+    int valid[NP];   // real columns among the four (0: padding or beyond the row)
+};
+
+template <int NP>
+__device__ __forceinline__ void lane_cols(const DescDev& d, const StoreView& v, int lane, LaneCols<NP>& lc)
+{
+    const int W4 = v.W >> 2, A = d.n_theta * d.n_ang_r;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int c4 = lane + 32 * p;
+        const int col = 4 * c4;
+        int valid;
+        if (col < v.Rp) {
+            lc.loc[p] = col;
+            lc.spc[p] = -1;
+            valid = d.n_rad - col;
+        } else {
+            const int ww = col - v.Rp;
+            const int sp = ww / v.Ap;
+            lc.loc[p] = ww - sp * v.Ap;
+            lc.spc[p] = sp;
+            valid = A - lc.loc[p];
+        }
+        valid = valid < 0 ? 0 : (valid > 4 ? 4 : valid);
+        lc.valid[p] = c4 < W4 ? valid : 0;
+    }
+}
+
+__device__ __forceinline__ int lane_gcol(const DescDev& d, int sj, int loc, int spc)
+{
+    if (spc < 0) return sj * d.n_rad + loc;
+    const int a = sj < spc ? sj : spc, b = sj < spc ? spc : sj;
+    return d.rad_cols + pair_block_s(a, b, d.S) * (d.n_theta * d.n_ang_r) + loc;
+}
+
+template <int NP, bool VEC>
+__global__ void __launch_bounds__(kStoreWarps * 32, NP <= 3 ? 3 : 2)
+k_store_adjoint_b(StoreView v, DescDev d, const float* __restrict__ g_rows, float* __restrict__ F,
+                  float* __restrict__ vir_atom)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t T = (int64_t)gridDim.x * kStoreWarps;
+    const int64_t w = (int64_t)blockIdx.x * kStoreWarps + warp;
+    const int64_t a0 = range_start(v, w, T), a1 = range_start(v, w + 1, T);
+    if (a0 >= a1) return;
+    LaneCols<NP> lc;
+    lane_cols<NP>(d, v, lane, lc);
+    const int W4 = v.W >> 2;
+    for (int64_t i = a0; i < a1; ++i) {
+        const float* gi = g_rows + (size_t)v.row_of_atom[i] * d.D;
+        const int64_t e0 = v.ent_off[i], e1 = v.ent_off[i + 1];
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        float vir[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) vir[k] = 0.f;
+        for (int64_t e = e0; e < e1; ++e) {
+            const int2 id = v.ent_idx[e];
+            const float4* J0 = reinterpret_cast<const float4*>(v.jac + (size_t)e * 3 * v.W);
+            float4 x[NP][3];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int c4 = lane + 32 * p;
+                if (c4 < W4) {
+                    x[p][0] = __ldcs(J0 + c4);
+                    x[p][1] = __ldcs(J0 + W4 + c4);
+                    x[p][2] = __ldcs(J0 + 2 * W4 + c4);
+                } else {
+                    x[p][0] = x[p][1] = x[p][2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int valid = lc.valid[p];
+                float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (valid > 0) {
+                    const int gcol = lane_gcol(d, id.y, lc.loc[p], lc.spc[p]);
+                    if (VEC) {
+                        gv = *reinterpret_cast<const float4*>(gi + gcol);
+                    } else {
+                        gv.x = gi[gcol];
+                        if (valid > 1) gv.y = gi[gcol + 1];
+                        if (valid > 2) gv.z = gi[gcol + 2];
+                        if (valid > 3) gv.w = gi[gcol + 3];
+                    }
+                }
+                q0 = fmaf(x[p][0].x, gv.x, fmaf(x[p][0].y, gv.y, fmaf(x[p][0].z, gv.z, fmaf(x[p][0].w, gv.w, q0))));
+                q1 = fmaf(x[p][1].x, gv.x, fmaf(x[p][1].y, gv.y, fmaf(x[p][1].z, gv.z, fmaf(x[p][1].w, gv.w, q1))));
+                q2 = fmaf(x[p][2].x, gv.x, fmaf(x[p][2].y, gv.y, fmaf(x[p][2].z, gv.z, fmaf(x[p][2].w, gv.w, q2))));
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+                q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+                q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&F[3 * (int64_t)id.x + 0], -q0);
+                atomicAdd(&F[3 * (int64_t)id.x + 1], -q1);
+                atomicAdd(&F[3 * (int64_t)id.x + 2], -q2);
+            }
+            fx += q0; fy += q1; fz += q2;
+            if (vir_atom) {
+                const float4 r = v.ent_vec[e];
+                const float q[3] = {q0, q1, q2}, rv[3] = {r.x, r.y, r.z};
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) vir[3 * a + b] -= q[a] * rv[b];
+            }
+        }
+        if (lane == 0 && e1 > e0) {
+            atomicAdd(&F[3 * i + 0], fx);
+            atomicAdd(&F[3 * i + 1], fy);
+            atomicAdd(&F[3 * i + 2], fz);
+        }
+        if (vir_atom && lane < 9) {
+            float val = vir[0];
+#pragma unroll
+            for (int k = 1; k < 9; ++k) if (lane == k) val = vir[k];
+            vir_atom[9 * i + lane] = val;
+        }
+    }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kStoreWarps * 32, NP <= 3 ? 3 : 2)
+k_store_tangent_b(StoreView v, DescDev d, const float* __restrict__ u, float* __restrict__ wd)
+{
+    extern __shared__ float smf[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t T = (int64_t)gridDim.x * kStoreWarps;
+    const int64_t w = (int64_t)blockIdx.x * kStoreWarps + warp;
+    const int64_t a0 = range_start(v, w, T), a1 = range_start(v, w + 1, T);
+    if (a0 >= a1) return;
+    LaneCols<NP> lc;
+    lane_cols<NP>(d, v, lane, lc);
+    const int W4 = v.W >> 2, D = d.D;
+    float* t = smf + (size_t)warp * ((D + 3) & ~3);
+    for (int c = lane; c < D; c += 32) t[c] = 0.f;
+    __syncwarp();
+    for (int64_t i = a0; i < a1; ++i) {
+        const float uix = u[3 * i], uiy = u[3 * i + 1], uiz = u[3 * i + 2];
+        const int64_t e0 = v.ent_off[i], e1 = v.ent_off[i + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            const int2 id = v.ent_idx[e];
+            const int64_t j = id.x;
+            const float4* J0 = reinterpret_cast<const float4*>(v.jac + (size_t)e * 3 * v.W);
+            float4 x[NP][3];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int c4 = lane + 32 * p;
+                if (c4 < W4) {
+                    x[p][0] = __ldcs(J0 + c4);
+                    x[p][1] = __ldcs(J0 + W4 + c4);
+                    x[p][2] = __ldcs(J0 + 2 * W4 + c4);
+                } else {
+                    x[p][0] = x[p][1] = x[p][2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            const float vx = u[3 * j] - uix, vy = u[3 * j + 1] - uiy, vz = u[3 * j + 2] - uiz;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int valid = lc.valid[p];
+                if (valid > 0) {
+                    const int gcol = lane_gcol(d, id.y, lc.loc[p], lc.spc[p]);
+                    t[gcol] += fmaf(x[p][0].x, vx, fmaf(x[p][1].x, vy, x[p][2].x * vz));
+                    if (valid > 1) t[gcol + 1] += fmaf(x[p][0].y, vx, fmaf(x[p][1].y, vy, x[p][2].y * vz));
+                    if (valid > 2) t[gcol + 2] += fmaf(x[p][0].z, vx, fmaf(x[p][1].z, vy, x[p][2].z * vz));
+                    if (valid > 3) t[gcol + 3] += fmaf(x[p][0].w, vx, fmaf(x[p][1].w, vy, x[p][2].w * vz));
+                }
+            }
+            __syncwarp();   // the next entry may map other lanes onto these columns
+        }
+        float* out = wd + (size_t)v.row_of_atom[i] * D;
+        for (int c = lane; c < D; c += 32) {
+            out[c] = t[c];
+            t[c] = 0.f;
+        }
+        __syncwarp();
+    }
+}
+
+// resident CTAs of a kernel instance on this device, times the SM count, capped by the work
+template <class K>
+static unsigned balanced_blocks(K kernel, size_t smem, int64_t N)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kStoreWarps * 32, smem);
+    int64_t nb = (int64_t)(sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    const int64_t need = (N + kStoreWarps - 1) / kStoreWarps;
+    return (unsigned)(nb < need ? nb : need);
+}
+
+template <int NP, bool VEC>
+static cudaError_t store_adjoint_np(const StoreView& v, const DescDev& d, const float* g_rows, float* F,
+                                    float* vir_atom, cudaStream_t s)
+{
+    const unsigned nb = balanced_blocks(k_store_adjoint_b<NP, VEC>, 0, v.N);
+    k_store_adjoint_b<NP, VEC><<<nb, kStoreWarps * 32, 0, s>>>(v, d, g_rows, F, vir_atom);
+    return cudaGetLastError();
+}
+
+template <int NP>
+static cudaError_t store_tangent_np(const StoreView& v, const DescDev& d, const float* u, float* wd, cudaStream_t s)
+{
+    const size_t smem = (size_t)kStoreWarps * ((d.D + 3) & ~3) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_store_tangent_b<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned nb = balanced_blocks(k_store_tangent_b<NP>, smem, v.N);
+    k_store_tangent_b<NP><<<nb, kStoreWarps * 32, smem, s>>>(v, d, u, wd);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_store_adjoint(const StoreView& v, const DescDev& d, const float* g_rows, float* F, float* vir_atom,
                                  cudaStream_t s, int* launches)
 {
     const unsigned nb = (unsigned)((v.N + kStoreWarps - 1) / kStoreWarps);
     if (nb == 0) return cudaSuccess;
     const bool vec = d.n_rad % 4 == 0 && (d.n_theta * d.n_ang_r) % 4 == 0;
+    const int np = (v.W / 4 + 31) / 32;
+    if (np <= 6) {
+        ++*launches;
+        switch (np * 2 + (vec ? 1 : 0)) {
+            case 2: return store_adjoint_np<1, false>(v, d, g_rows, F, vir_atom, s);
+            case 3: return store_adjoint_np<1, true>(v, d, g_rows, F, vir_atom, s);
+            case 4: return store_adjoint_np<2, false>(v, d, g_rows, F, vir_atom, s);
+            case 5: return store_adjoint_np<2, true>(v, d, g_rows, F, vir_atom, s);
+            case 6: return store_adjoint_np<3, false>(v, d, g_rows, F, vir_atom, s);
+            case 7: return store_adjoint_np<3, true>(v, d, g_rows, F, vir_atom, s);
+            case 8: return store_adjoint_np<4, false>(v, d, g_rows, F, vir_atom, s);
+            case 9: return store_adjoint_np<4, true>(v, d, g_rows, F, vir_atom, s);
+            case 10: return store_adjoint_np<5, false>(v, d, g_rows, F, vir_atom, s);
+            case 11: return store_adjoint_np<5, true>(v, d, g_rows, F, vir_atom, s);
+            case 12: return store_adjoint_np<6, false>(v, d, g_rows, F, vir_atom, s);
+            default: return store_adjoint_np<6, true>(v, d, g_rows, F, vir_atom, s);
+        }
+    }
+    // wider rows: one warp per atom, columns in a loop
     if (vec) k_store_adjoint<true><<<nb, kStoreWarps * 32, 0, s>>>(v, d, g_rows, F, vir_atom);
     else k_store_adjoint<false><<<nb, kStoreWarps * 32, 0, s>>>(v, d, g_rows, F, vir_atom);
     ++*launches;
@@ -430,6 +691,19 @@ cudaError_t launch_store_tangent(const StoreView& v, const DescDev& d, const flo
 {
     if (v.N == 0) return cudaSuccess;
     const size_t row = (size_t)((d.D + 3) & ~3) * sizeof(float);
+    const int np = (v.W / 4 + 31) / 32;
+    if (np <= 6 && row * kStoreWarps <= 200 * 1024) {
+        ++*launches;
+        switch (np) {
+            case 1: return store_tangent_np<1>(v, d, u, wdot_rows, s);
+            case 2: return store_tangent_np<2>(v, d, u, wdot_rows, s);
+            case 3: return store_tangent_np<3>(v, d, u, wdot_rows, s);
+            case 4: return store_tangent_np<4>(v, d, u, wdot_rows, s);
+            case 5: return store_tangent_np<5>(v, d, u, wdot_rows, s);
+            default: return store_tangent_np<6>(v, d, u, wdot_rows, s);
+        }
+    }
+    // wider rows or descriptors: one warp per atom, columns in a loop
     int warps = (int)((200 * 1024) / row);
     warps = warps > kStoreWarps ? kStoreWarps : warps;
     if (warps < 1) return cudaErrorInvalidValue;
