@@ -9,6 +9,7 @@ first time it is needed (or by :func:`build`) into ``oracle/_build/``.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 from typing import Optional, Sequence
@@ -347,3 +348,133 @@ def sampled(system, cfg: int, desc, archs, theta, samples: Sequence[int], cap: i
     if np.any(nnb > cap):
         raise RuntimeError("neighbour capacity %d exceeded" % cap)
     return dict(nnb=nnb, nb_j=nbj, nb_shift=nbs, G=G, E=E, F=F)
+
+
+# ------------------------------------------------------------------ charge equilibration
+
+KE_EV_A = 14.399645478425668     # e^2 / (4 pi eps_0) in eV A
+
+
+def _act(t, z):
+    return np.exp(-z * z) if t == 1 else (np.maximum(z, 0.0) if t == 2 else (np.tanh(z) if t == 3 else z))
+
+
+def _act_d1(t, z):
+    if t == 1:
+        return -2.0 * z * np.exp(-z * z)
+    if t == 2:
+        return (z > 0.0).astype(np.float64)
+    if t == 3:
+        return 1.0 - np.tanh(z) ** 2
+    return np.ones_like(z)
+
+
+def mlp_rows(arch, theta_s, X, seeds=None):
+    """Eq. 1 on the rows of X (any output width): returns the outputs [n, w_L] and, with
+    seeds [n, w_L], the input gradient sum_k seeds_k d out_k / dX."""
+    X = np.atleast_2d(np.asarray(X, np.float64))
+    Ws, bs, o = [], [], 0
+    for l in range(arch.n_layers):
+        fi, fo = arch.widths[l], arch.widths[l + 1]
+        Ws.append(np.asarray(theta_s[o:o + fo * fi]).reshape(fo, fi))
+        o += fo * fi
+        bs.append(np.asarray(theta_s[o:o + fo]))
+        o += fo
+    a, zs = X, []
+    for l in range(arch.n_layers):
+        z = a @ Ws[l].T + bs[l]
+        zs.append(z)
+        a = _act(arch.acts[l], z)
+    if seeds is None:
+        return a
+    bar = np.asarray(seeds, np.float64)
+    for l in range(arch.n_layers - 1, -1, -1):
+        bar = (bar * _act_d1(arch.acts[l], zs[l])) @ Ws[l]
+    return a, bar
+
+
+def qeq_kernel(r, sig_i, sig_j, ke=KE_EV_A):
+    """Interaction of two unit Gaussian charges of widths sig_i, sig_j at distance r > 0, and
+    its derivative with respect to r (scalars)."""
+    g = math.sqrt(2.0 * (sig_i ** 2 + sig_j ** 2))
+    e = math.erf(r / g)
+    K = ke * e / r
+    dK = ke * (2.0 / math.sqrt(math.pi) * math.exp(-(r / g) ** 2) / (g * r) - e / r ** 2)
+    return K, dK
+
+
+def qeq_solve(pos, sigma, chi, hard, Q, ke=KE_EV_A):
+    """Charges of one configuration: the stationary point of
+        E(q) = sum_i (chi_i q_i + J_i q_i^2 / 2) + 1/2 sum_ij q_i q_j K_ij
+    subject to sum_i q_i = Q, with K_ij the Gaussian-charge interaction and K_ii the self
+    energy ke / (sigma_i sqrt(pi)).  Solved as the (n+1) x (n+1) linear system
+    [A 1; 1^T 0] [q; lam] = [-chi; Q], A = diag(J) + K.  Returns q, lam, K."""
+    pos = np.asarray(pos, np.float64)
+    n = len(pos)
+    K = np.zeros((n, n))
+    for i in range(n):
+        K[i, i] = ke / (sigma[i] * math.sqrt(math.pi))
+        for j in range(n):
+            if j != i:
+                K[i, j] = qeq_kernel(np.linalg.norm(pos[i] - pos[j]), sigma[i], sigma[j], ke)[0]
+    M = np.zeros((n + 1, n + 1))
+    M[:n, :n] = K + np.diag(hard)
+    M[:n, n] = 1.0
+    M[n, :n] = 1.0
+    rhs = np.concatenate([-np.asarray(chi, np.float64), [Q]])
+    x = np.linalg.solve(M, rhs)
+    return x[:n], x[n], K
+
+
+def qeq_batch(system, desc, archs, theta, qeq, charge=None, ke=KE_EV_A):
+    """Energies, charges and forces with the charge-equilibration layer (Sec. II.B): every
+    atom's network gives (e_i, dchi_i, dJ_i); chi_i = chi0_s + dchi_i, J_i = J0_s + dJ_i; the
+    charges solve the constrained stationarity of qeq_solve for each (non-periodic)
+    configuration, and
+        E_c = sum_i (e_i + chi_i q_i + J_i q_i^2 / 2) + 1/2 sum_ij q_i q_j K_ij.
+    Forces are -dE/dx at the equilibrated charges (the constraint's multiplier absorbs the
+    charges' response): the networks' input gradients with seeds (1, q_i, q_i^2 / 2) through
+    the descriptor Jacobians, plus the Gaussian-charge pair forces.
+    E_atom_i = e_i + chi_i q_i + J_i q_i^2 / 2 + q_i (K q)_i / 2."""
+    s = system
+    G = batch(s, desc, archs, theta, want_G=True)["G"]
+    toff = _theta_off(archs)
+    N = s.n_atoms
+    out3 = np.zeros((N, 3))
+    for sp in range(len(archs)):
+        rows = np.nonzero(s.species == sp)[0]
+        if len(rows):
+            out3[rows] = mlp_rows(archs[sp], theta[toff[sp]:toff[sp + 1]], G[rows])
+    sig = np.asarray(qeq["sigma"])[s.species]
+    chi = np.asarray(qeq["chi0"])[s.species] + out3[:, 1]
+    hard = np.asarray(qeq["hard0"])[s.species] + out3[:, 2]
+    q = np.zeros(N)
+    E_atom = np.zeros(N)
+    F = np.zeros((N, 3))
+    lam = np.zeros(s.n_cfg)
+    for c in range(s.n_cfg):
+        a0, a1 = int(s.atom_off[c]), int(s.atom_off[c + 1])
+        if a1 == a0:
+            continue
+        Qc = 0.0 if charge is None else float(charge[c])
+        qc, lam[c], K = qeq_solve(s.pos[a0:a1], sig[a0:a1], chi[a0:a1], hard[a0:a1], Qc, ke)
+        q[a0:a1] = qc
+        E_atom[a0:a1] = out3[a0:a1, 0] + chi[a0:a1] * qc + 0.5 * hard[a0:a1] * qc ** 2 + 0.5 * qc * (K @ qc)
+        for i in range(a0, a1):
+            for j in range(a0, a1):
+                if i != j:
+                    d = s.pos[i] - s.pos[j]
+                    r = np.linalg.norm(d)
+                    F[i] -= q[i] * q[j] * qeq_kernel(r, sig[i], sig[j], ke)[1] * d / r
+    seeds = np.stack([np.ones(N), q, 0.5 * q ** 2], 1)
+    g = np.zeros_like(G)
+    for sp in range(len(archs)):
+        rows = np.nonzero(s.species == sp)[0]
+        if len(rows):
+            g[rows] = mlp_rows(archs[sp], theta[toff[sp]:toff[sp + 1]], G[rows], seeds[rows])[1]
+    jac = jacobians(s, desc)
+    qe = np.einsum("ed,edc->ec", g[jac["i"]], jac["J"])
+    np.add.at(F, jac["i"], qe)
+    np.add.at(F, jac["j"], -qe)
+    E_cfg = np.array([E_atom[int(s.atom_off[c]):int(s.atom_off[c + 1])].sum() for c in range(s.n_cfg)])
+    return dict(E_cfg=E_cfg, E_atom=E_atom, q=q, F=F, lam=lam, chi=chi, hard=hard, out=out3)

@@ -135,6 +135,10 @@ class Workload:
     f_ref: Optional[np.ndarray] = None   # float64 [N,3]
     w_force: float = 0.1
     seed: int = 0
+    # charge equilibration (3-output networks): per-species Gaussian widths, reference
+    # electronegativities and hardnesses, and the total charge of every configuration
+    qeq: Optional[dict] = None
+    charge: Optional[np.ndarray] = None
 
     @property
     def param_offsets(self) -> np.ndarray:
@@ -470,6 +474,54 @@ def carbon16(seed: int = 0, replicas: int = 1) -> Workload:
                     mlp_bf16=False, seed=seed)
 
 
+def nacl(seed: int = 0, n_clusters: int = 2) -> Workload:
+    """Charged sodium chloride clusters shaped like those of Sec. III.C: Na9Cl8+ (a 3 x 3 x 2
+    rock-salt block, a = 5.64 A, with one Cl removed) and Na8Cl8+ (a corner Na removed as
+    well), alternating, each with total charge +1, displaced by sigma = 0.1 A and rotated at
+    random; no periodicity.  Species Na = 0, Cl = 1.  Descriptor of size 45 (9 radial shells
+    per species, 3 theta x 3 R angular bins), rc = 6 A; networks 45-15-15-3 (local energy,
+    electronegativity and hardness corrections).  Charge-equilibration constants: Gaussian
+    widths 1.0 / 1.2 A and reference electronegativity / hardness from the atoms' Mulliken
+    values (2.85 / 8.30 eV and 4.59 / 9.35 eV)."""
+    rng = np.random.default_rng(seed)
+    a, rc = 5.64, 6.0
+    sites, spec = [], []
+    for i in range(3):
+        for j in range(3):
+            for k in range(2):
+                sites.append([i, j, k])
+                spec.append((i + j + k) % 2)     # Na on even sites: 9 Na, 9 Cl
+    sites = np.array(sites, np.float64) * (a / 2)
+    spec = np.array(spec, np.int32)
+    cl = np.nonzero(spec == 1)[0]
+    drop_cl = cl[len(cl) // 2]                    # a central-layer Cl
+    na9 = np.array([q for q in range(len(spec)) if q != drop_cl])
+    na8 = na9[1:]                                  # the corner Na at the origin as well
+    pos_all, spec_all, off = [], [], [0]
+    for c in range(n_clusters):
+        keep = na9 if c % 2 == 0 else na8
+        x = sites[keep] - sites[keep].mean(0)
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        x = x @ q.T + rng.normal(0.0, 0.1, size=x.shape) + rng.uniform(-20, 20, size=3)
+        pos_all.append(x)
+        spec_all.append(spec[keep])
+        off.append(off[-1] + len(keep))
+    C = n_clusters
+    sysm = System(np.asarray(off, np.int64), np.concatenate(pos_all), np.concatenate(spec_all),
+                  np.zeros((C, 9)), np.zeros((C, 3), np.uint8), 2)
+    desc = descriptor_params(2, rc, 9, 3, 3, eta_rad=2.0, eta_ang=1.5, zeta=4.0)
+    archs = [MLPArch((desc.D, 15, 15, 3), (ACT_GAUSSIAN, ACT_GAUSSIAN, ACT_LINEAR)) for _ in range(2)]
+    theta = init_weights(rng, desc, archs, *GAINS["nacl"])
+    # small output layers: corrections of O(0.1) to the reference constants
+    off_p = param_offsets(archs)
+    for sp in range(2):
+        o = off_p[sp] + 45 * 15 + 15 + 15 * 15 + 15
+        theta[o:o + 3 * 15 + 3] *= 0.2
+    qeq = dict(sigma=np.array([1.0, 1.2]), chi0=np.array([2.85, 8.30]), hard0=np.array([4.59, 9.35]))
+    return Workload("nacl%d" % n_clusters, sysm, desc, archs, theta, mlp_bf16=False, seed=seed, qeq=qeq,
+                    charge=np.ones(C))
+
+
 GAINS = {
     "diamond64": (3.5, 4.5),
     "molecules1024": (4.0, 2.0),
@@ -477,6 +529,7 @@ GAINS = {
     "fcc1m": (0.9, 0.9),
     "ragged4096": (3.5, 2.2),
     "carbon16": (0.7, 0.1),
+    "nacl": (0.6, 0.4),
 }
 
 
@@ -497,5 +550,8 @@ def make(name: str, seed: int = 0) -> Workload:
         "carbon16": lambda: carbon16(seed),
         "carbon16x64": lambda: carbon16(seed, 64),
         "carbon16x4096": lambda: carbon16(seed, 4096),
+        "nacl2": lambda: nacl(seed, 2),
+        "nacl64": lambda: nacl(seed, 64),
+        "nacl4096": lambda: nacl(seed, 4096),
     }
     return table[name]()
