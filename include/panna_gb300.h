@@ -99,8 +99,9 @@ typedef struct {
 #define PANNA_MAX_LAYERS 8
 
 /*
- * One species' network (Eq. 1): widths[0] = D, widths[n_layers] = 1, act[l] is the
- * activation of layer l+1.  Parameters of a species, in order for l = 1..n_layers:
+ * One species' network (Eq. 1): widths[0] = D, widths[n_layers] = 1 (an atomic energy) or 3
+ * for every species (the three outputs of the charge-equilibration scheme of Sec. II.B, used
+ * only by panna_qeq_energy_forces), act[l] is the activation of layer l+1.  Parameters of a species, in order for l = 1..n_layers:
  * W_l (row-major [widths[l]][widths[l-1]]) then b_l [widths[l]]; layer l computes
  * z = W_l a + b_l.  The flat parameter vector of the model is the concatenation over
  * species 0..S-1 (FP32).
@@ -376,6 +377,47 @@ panna_status panna_loss_grad(panna_ctx* ctx, const panna_system* sys, const floa
                              const double* E_ref, const float* F_ref, double w_force,
                              double* loss, float* dtheta, double* E_cfg, float* F,
                              panna_stream_t stream);
+
+/*
+ * Long-range electrostatics by charge equilibration (Sec. II.B).  The networks have three
+ * outputs per atom (created with widths[n_layers] = 3): a local energy e_i and corrections to
+ * the electronegativity and hardness of the atom's species, chi_i = chi0[s] + out_1 and
+ * J_i = hard0[s] + out_2 (the second-order expansion of the energy in the atomic charge).
+ * The paper defers the electrostatic form to its reference; this library takes Gaussian
+ * charge distributions of per-species width sigma[s]:
+ *     E_c = sum_i (e_i + chi_i q_i + J_i q_i^2 / 2) + 1/2 sum_ij q_i q_j K_ij,
+ *     K_ij = k erf(r_ij / g_ij) / r_ij, g_ij = sqrt(2 (sigma_i^2 + sigma_j^2)),
+ *     K_ii = k / (sigma_i sqrt(pi)),
+ * and the charges q of each configuration are the stationary point of E_c under
+ * sum_i q_i = Q_c (the linear system [A 1; 1^T 0][q; lam] = [-chi; Q_c], A = diag(J) + K,
+ * solved in FP64 with partial pivoting).  Forces are -dE_c/dx at those charges.  Direct
+ * sums over all pairs of a configuration: non-periodic configurations of at most 128 atoms
+ * (clusters, molecules; PANNA_ERR_UNSUPPORTED otherwise).  Units: A, e, eV;
+ * k_coulomb = 0 selects 14.399645478425668 eV A / e^2.
+ */
+typedef struct {
+    const double* sigma;   /* [n_species] Gaussian charge widths (A), > 0, host */
+    const double* chi0;    /* [n_species] reference electronegativities (eV / e), host */
+    const double* hard0;   /* [n_species] reference hardnesses (eV / e^2), host */
+    double k_coulomb;      /* eV A / e^2; 0 = the SI value */
+} panna_qeq_params;
+
+/* Set the constants above (copied); the context's networks must have 3 outputs. */
+panna_status panna_set_qeq(panna_ctx* ctx, const panna_qeq_params* params);
+
+/*
+ * Energies, charges and forces with charge equilibration.  total_charge [n_cfg] FP64 device
+ * (NULL = neutral configurations); outputs (device): E_cfg [n_cfg] FP64, E_atom [n_atoms]
+ * FP32 (may be NULL; E_atom_i = e_i + chi_i q_i + J_i q_i^2/2 + q_i (K q)_i / 2), charges
+ * [n_atoms] FP64 (may be NULL), F [n_atoms*3] FP32.  FP32 networks.  A singular system
+ * returns PANNA_ERR_BAD_INPUT naming the configuration.  Follows panna_set_async like the
+ * other compute calls; with profiling on, the stages are "neighbors", "descriptor", "mlp"
+ * (forward), "forces" (the charge solve, energies and pair forces), "adjoint" (input
+ * gradient and descriptor adjoint) and "loss" (per-configuration sums).
+ */
+panna_status panna_qeq_energy_forces(panna_ctx* ctx, const panna_system* sys, const float* theta,
+                                     const double* total_charge, double* E_cfg, float* E_atom,
+                                     double* charges, float* F, panna_stream_t stream);
 
 /*
  * Precomputed descriptors with stored Jacobians (Sec. II.A: descriptors can be computed

@@ -86,6 +86,8 @@ struct panna_ctx {
     bool frozen[kMaxSpecies][kMaxLayers] = {};
     int last_launches = 0;
     DescGrid64 g64{};                 // FP64 descriptor parameters (stored Jacobians)
+    QeqDev qeq{};                     // charge-equilibration constants (3-output networks)
+    bool qeq_set = false;
     // autotuner: kernel variant per problem signature, measured on the first call
     struct Tuned { int64_t N, C; int cap, prec; int variant[3]; };   // -1 = not measured yet
     Tuned tuned[16];
@@ -513,6 +515,8 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
 panna_status run(panna_ctx* c, const panna_system* sys, const Request& rq, cudaStream_t s)
 {
     ST(check_system(c, sys, rq.store == nullptr));
+    if (c->plan.n_out != 1 && !rq.G_out)
+        return fail(PANNA_ERR_UNSUPPORTED, "networks with 3 outputs serve panna_qeq_energy_forces only");
     CU(cudaSetDevice(c->device));
     const bool train = rq.train || rq.vjp;
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -639,10 +643,11 @@ panna_status panna_create(const panna_desc_params* p, int32_t n_archs, const pan
             delete c;
             return fail(PANNA_ERR_UNSUPPORTED, "every species needs the same number of layers (1..%d)", kMaxLayers);
         }
-        if (a.widths[0] != D || a.widths[a.n_layers] != 1) {
+        const int n_out = archs[0].widths[archs[0].n_layers];
+        if (a.widths[0] != D || (n_out != 1 && n_out != 3) || a.widths[a.n_layers] != n_out) {
             delete c;
-            return fail(PANNA_ERR_INVALID_ARG, "species %d: input width must be D=%lld and output width 1", s,
-                        (long long)D);
+            return fail(PANNA_ERR_INVALID_ARG, "species %d: input width must be D=%lld and every species' output "
+                        "width 1 (energy) or 3 (charge equilibration)", s, (long long)D);
         }
         for (int l = 0; l < a.n_layers; ++l) {
             if (a.widths[l + 1] < 1 || a.widths[l + 1] > 1024 || a.act[l] < 0 || a.act[l] > 3) {
@@ -656,9 +661,10 @@ panna_status panna_create(const panna_desc_params* p, int32_t n_archs, const pan
             pl.b_off[s][l] = off;
             off += a.widths[l + 1];
         }
-        pl.widths[s][a.n_layers] = 1;
+        pl.widths[s][a.n_layers] = a.widths[a.n_layers];
     }
     pl.P = off;
+    pl.n_out = archs[0].widths[archs[0].n_layers];
     pl.max_hidden = 1;
     for (int l = 0; l <= pl.L; ++l) {
         int m = 0;
@@ -747,6 +753,7 @@ panna_status panna_md_run(panna_ctx* c, const panna_system* sys, double* vel, co
         return fail(PANNA_ERR_INVALID_ARG, "dt must be > 0; temperature, friction and skin >= 0");
     if (prec < PANNA_MLP_FP32 || prec > PANNA_MLP_BF16_FAST) return fail(PANNA_ERR_INVALID_ARG, "unknown precision");
     if (sys->ghost) return fail(PANNA_ERR_UNSUPPORTED, "dynamics of a batch with ghost atoms");
+    if (c->plan.n_out != 1) return fail(PANNA_ERR_UNSUPPORTED, "dynamics with 3-output networks");
     MdSpecies ms{};
     for (int sp = 0; sp < c->d.S; ++sp) {
         if (!(p->mass[sp] > 0.0)) return fail(PANNA_ERR_INVALID_ARG, "mass of species %d must be > 0", sp);
@@ -954,6 +961,95 @@ panna_status panna_loss_grad(panna_ctx* c, const panna_system* sys, const float*
     rq.theta = theta; rq.train = true; rq.E_ref = E_ref; rq.F_ref = F_ref; rq.w_force = w_force; rq.loss = loss;
     rq.dtheta = dtheta; rq.E_cfg = E_cfg; rq.F = F; rq.forces = true; rq.energy = true;
     return run(c, sys, rq, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ charge equilibration
+
+panna_status panna_set_qeq(panna_ctx* c, const panna_qeq_params* p)
+{
+    if (!c || !p || !p->sigma || !p->chi0 || !p->hard0) return fail(PANNA_ERR_INVALID_ARG, "null argument");
+    if (c->plan.n_out != 3) return fail(PANNA_ERR_INVALID_ARG, "charge equilibration needs networks with 3 outputs");
+    if (!(p->k_coulomb >= 0.0)) return fail(PANNA_ERR_INVALID_ARG, "k_coulomb must be >= 0");
+    QeqDev q{};
+    for (int s = 0; s < c->d.S; ++s) {
+        if (!(p->sigma[s] > 0.0) || !std::isfinite(p->chi0[s]) || !std::isfinite(p->hard0[s]))
+            return fail(PANNA_ERR_INVALID_ARG, "species %d: sigma must be > 0, chi0 and hard0 finite", s);
+        q.sigma[s] = p->sigma[s];
+        q.chi0[s] = p->chi0[s];
+        q.hard0[s] = p->hard0[s];
+    }
+    q.ke = p->k_coulomb > 0.0 ? p->k_coulomb : 14.399645478425668;
+    c->qeq = q;
+    c->qeq_set = true;
+    return PANNA_OK;
+}
+
+panna_status panna_qeq_energy_forces(panna_ctx* c, const panna_system* sys, const float* theta,
+                                     const double* total_charge, double* E_cfg, float* E_atom, double* charges,
+                                     float* F, panna_stream_t stream)
+{
+    ST(check_system(c, sys));
+    if (!theta || !E_cfg || !F) return fail(PANNA_ERR_INVALID_ARG, "theta, E_cfg and F are required");
+    if (c->plan.n_out != 3 || !c->qeq_set)
+        return fail(PANNA_ERR_INVALID_ARG, "needs 3-output networks and panna_set_qeq");
+    if (sys->ghost) return fail(PANNA_ERR_UNSUPPORTED, "charge equilibration of a batch with ghost atoms");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(c->device));
+    const int64_t N = sys->n_atoms;
+    const bool acc = c->ang_mode != 2;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        Layout L;
+        ST(prepare(c, sys, false, false, L, s));
+        int& nl = c->last_launches;
+        nl = 0;
+        for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
+        c->n_marked = 0;
+        CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
+        stage_mark(c, 0, s);
+        CU(build_neighbors(L.w, c->d, s, &nl));
+        CU(species_order(L.w, c->d.S, s, &nl));
+        CU(mlp_tiles(c->plan, L.w.seg_off, L.mb.tile_start, s, &nl));
+        stage_mark(c, 1, s);
+        int dummy = 0;
+        const int vd = tuned_variant(c, sys, PANNA_MLP_FP32, KV_DESC, s, [&](int vv) {
+            launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &dummy, vv);
+        });
+        CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl, vd));
+        stage_mark(c, 2, s);
+        CU(mlp_forward(c->plan, L.mb, theta, N, s, &nl));
+        // the charge-equilibration solve ("forces" stage): charges, energies, pair forces, seeds
+        stage_mark(c, 4, s);
+        const int ldL = c->plan.ld[c->plan.L];
+        CU(cudaMemsetAsync(F, 0, sizeof(float) * 3 * N, s));
+        CU(launch_qeq(c->qeq, L.w, L.mb.A[c->plan.L], ldL, total_charge, L.E_rows, charges, F, L.mb.Ab, ldL, s,
+                      &nl));
+        stage_mark(c, 3, s);
+        CU(mlp_input_grad(c->plan, L.mb, theta, N, L.g, s, &nl, nullptr, true));
+        const int va = tuned_variant(c, sys, PANNA_MLP_FP32, KV_ADJ, s, [&](int vv) {
+            launch_adjoint(L.w, c->d, L.g, L.F_tune, nullptr, acc, vv, s, &dummy);
+        });
+        CU(launch_adjoint(L.w, c->d, L.g, F, nullptr, acc, va, s, &nl));
+        stage_mark(c, 7, s);
+        CU(launch_cfg_reduce(L.w, L.E_rows, nullptr, E_cfg, nullptr, E_atom, L.cfg_part, s, &nl));
+        if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
+        CU(cudaGetLastError());
+        if (c->async) return PANNA_OK;
+        int need = 0;
+        panna_status st = collect(c, L, s, &need);
+        finish_profile(c);
+        if (st == PANNA_ERR_NEIGHBOR_OVERFLOW && attempt == 0) {
+            c->cap = need + need / 4 + 8;
+            continue;
+        }
+        if (st == PANNA_ERR_UNSUPPORTED)
+            return fail(PANNA_ERR_UNSUPPORTED, "configuration %d: charge equilibration takes non-periodic "
+                        "configurations of at most %d atoms", c->h_status->bad_index, kQeqMax);
+        if (st == PANNA_ERR_BAD_INPUT && c->h_status->code == PANNA_ERR_BAD_INPUT)
+            return fail(PANNA_ERR_BAD_INPUT, "configuration or atom %d: invalid input or singular "
+                        "charge-equilibration system", c->h_status->bad_index);
+        return st;
+    }
+    return PANNA_OK;
 }
 
 // ------------------------------------------------------------------ stored descriptors

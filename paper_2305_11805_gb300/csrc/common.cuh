@@ -161,6 +161,18 @@ cudaError_t launch_store_tangent(const StoreView& v, const DescDev& d, const flo
 constexpr int kStoreMaxCap = 2048;
 constexpr int kStoreMaxD = 49152;
 
+// Charge equilibration (qeq.cu): per-species Gaussian widths, reference electronegativity and
+// hardness, Coulomb constant; configurations of at most kQeqMax atoms
+constexpr int kQeqMax = 128;
+struct QeqDev { double sigma[kMaxSpecies], chi0[kMaxSpecies], hard0[kMaxSpecies]; double ke; };
+size_t qeq_smem_bytes(int max_n);
+// out: network outputs (rows, stride ldo, columns e, dchi, dJ); writes E_rows (row order),
+// charges (atom order, may be null), adds the pair forces to F, writes the seeds
+// (1, q, q^2/2) of the networks' input gradient (rows, stride lds)
+cudaError_t launch_qeq(const QeqDev& qp, const Work& w, const float* out, int ldo, const double* Qtot,
+                       float* E_rows, double* charges, float* F, float* seeds, int lds, cudaStream_t s,
+                       int* launches);
+
 // Langevin dynamics (md.cu): per species a = (eV/A)/m in A/fs^2 and the thermal velocity
 // scale sigma = sqrt(kB T a) in A/fs
 struct MdSpecies { double acc[kMaxSpecies]; double sigma[kMaxSpecies]; };

@@ -380,11 +380,13 @@ cudaError_t mlp_forward(const MlpPlan& p, const MlpBuffers& b, const float* thet
 }
 
 cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, float* g,
-                           cudaStream_t s, int* launches, float** ab1)
+                           cudaStream_t s, int* launches, float** ab1, bool seeded)
 {
-    // seed dE/da_L = 1, then a_{l-1}bar = (a_l bar * act'(z_l)) W_l
-    k_seed<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, p.ld[p.L], nullptr, 0.f, b.Ab, nullptr);
-    ++*launches;
+    // seed dE/da_L = 1 (unless given), then a_{l-1}bar = (a_l bar * act'(z_l)) W_l
+    if (!seeded) {
+        k_seed<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, p.ld[p.L], nullptr, 0.f, b.Ab, nullptr);
+        ++*launches;
+    }
     float* cur = b.Ab;
     float* nxt = b.Ab2;
     const int lstop = ab1 ? 1 : 0;

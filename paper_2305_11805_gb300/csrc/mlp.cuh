@@ -26,6 +26,7 @@ struct MlpPlan {
     int ld[kMaxLayers + 1];   // row stride of layer-l activations = max width over species
     int64_t P;                // total parameters
     int max_hidden;           // max over l >= 1 of ld[l]
+    int n_out;                // output width: 1 (energy) or 3 (charge equilibration)
 };
 
 // Device buffers of one evaluation (rows in species order).
@@ -47,9 +48,10 @@ cudaError_t mlp_tiles(const MlpPlan& p, const int32_t* seg_off, int32_t* tile_st
 cudaError_t mlp_forward(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, cudaStream_t s, int* launches,
                         int l0 = 0);
 cudaError_t mlp_energy_rows(const MlpPlan& p, const MlpBuffers& b, int64_t N, float* E_rows, cudaStream_t s, int* launches);
-// g = dE/dG; with ab1 != nullptr the chain stops at dE/dA_1 (row stride ld[1]), returned in *ab1
+// g = dE/dG; with ab1 != nullptr the chain stops at dE/dA_1 (row stride ld[1]), returned in *ab1;
+// seeded: b.Ab already holds the output seeds (rows, stride ld[L]) instead of dE/da_L = 1
 cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, float* g,
-                           cudaStream_t s, int* launches, float** ab1 = nullptr);
+                           cudaStream_t s, int* launches, float** ab1 = nullptr, bool seeded = false);
 // BF16 tensor-core networks (mlp_tc.cu): energies and input gradients; ws from tc_workspace_bytes
 size_t tc_workspace_bytes(const MlpPlan& p, int64_t N, bool split);
 cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, void* ws,

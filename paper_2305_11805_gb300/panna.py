@@ -64,6 +64,10 @@ class panna_adam_params(C.Structure):
 PANNA_LOSS_QUADRATIC, PANNA_LOSS_EXPONENTIAL = 0, 1
 
 
+class panna_qeq_params(C.Structure):
+    _fields_ = [("sigma", _vp), ("chi0", _vp), ("hard0", _vp), ("k_coulomb", C.c_double)]
+
+
 class panna_store_info(C.Structure):
     _fields_ = [("n_atoms", C.c_int64), ("n_cfg", C.c_int64), ("n_entries", C.c_int64), ("D", C.c_int32),
                 ("width", C.c_int32), ("bytes", C.c_int64)]
@@ -121,6 +125,8 @@ def load(path: str = LIB_PATH):
         "panna_descriptors_static": (i32, [C.POINTER(panna_desc_params), C.POINTER(panna_system), _vp, _vp]),
         "panna_capture": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
         "panna_replay": (i32, [_vp, _vp]),
+        "panna_set_qeq": (i32, [_vp, C.POINTER(panna_qeq_params)]),
+        "panna_qeq_energy_forces": (i32, [_vp, C.POINTER(panna_system), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "panna_store_plan": (i32, [_vp, C.POINTER(panna_system), C.POINTER(panna_store_info), _vp]),
         "panna_store_sections": (i32, [_vp, C.POINTER(panna_store_info), C.POINTER(i64)]),
         "panna_store_build": (i32, [_vp, C.POINTER(panna_system), C.POINTER(panna_store_info), _vp, _vp]),
@@ -145,7 +151,8 @@ def exported_symbols() -> Sequence[str]:
             "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
             "panna_descriptors_static", "panna_capture", "panna_replay", "panna_store_plan",
-            "panna_store_sections", "panna_store_build", "panna_store_energy_forces", "panna_store_loss_grad"]
+            "panna_store_sections", "panna_store_build", "panna_store_energy_forces", "panna_store_loss_grad",
+            "panna_set_qeq", "panna_qeq_energy_forces"]
 
 
 def _check(status: int):
@@ -319,6 +326,18 @@ def panna_replay(ctx: int, stream=None):
     _check(load().panna_replay(ctx, _stream(stream)))
 
 
+def panna_set_qeq(ctx: int, sigma, chi0, hard0, k_coulomb: float = 0.0):
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (sigma, chi0, hard0)]
+    p = panna_qeq_params(arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data, float(k_coulomb))
+    _check(load().panna_set_qeq(ctx, C.byref(p)))
+
+
+def panna_qeq_energy_forces(ctx: int, sysd: "DeviceSystem", theta, total_charge, E_cfg, E_atom, charges, F,
+                            stream=None):
+    _check(load().panna_qeq_energy_forces(ctx, C.byref(sysd.s), _ptr(theta), _ptr(total_charge), _ptr(E_cfg),
+                                          _ptr(E_atom), _ptr(charges), _ptr(F), _stream(stream)))
+
+
 def panna_store_plan(ctx: int, sysd: "DeviceSystem", stream=None) -> panna_store_info:
     info = panna_store_info()
     _check(load().panna_store_plan(ctx, C.byref(sysd.s), C.byref(info), _stream(stream)))
@@ -436,6 +455,16 @@ class Potential:
         V = torch.empty((sysd.n_cfg, 3, 3), dtype=torch.float64, device="cuda") if virial else None
         panna_energy_forces(self.ctx, sysd, theta, prec, E, Ea, F, V)
         return E, Ea, F, V
+
+    def qeq_energy_forces(self, sysd: DeviceSystem, theta, total_charge=None):
+        """(E_cfg, E_atom, charges, F) with charge equilibration (panna_set_qeq first)."""
+        import torch
+        E = torch.empty(sysd.n_cfg, dtype=torch.float64, device="cuda")
+        Ea = torch.empty(sysd.n_atoms, dtype=torch.float32, device="cuda")
+        q = torch.empty(sysd.n_atoms, dtype=torch.float64, device="cuda")
+        F = torch.empty((sysd.n_atoms, 3), dtype=torch.float32, device="cuda")
+        panna_qeq_energy_forces(self.ctx, sysd, theta, total_charge, E, Ea, q, F)
+        return E, Ea, q, F
 
     def param_vjp(self, sysd: DeviceSystem, theta, dE=None, dF=None):
         import torch

@@ -1,0 +1,146 @@
+"""GPU parity of the charge-equilibration path (Sec. II.B) through the C ABI against the
+oracle: energies, atomic energies, charges and forces of NaCl clusters with a +1 total charge,
+per-configuration total charges, edge cases (an empty configuration, a lone atom, a dimer)
+and the argument checks."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2305_11805_gb300 import panna as P
+from paper_2305_11805_gb300 import workloads as W
+from tests import gpu_common as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_11805_gb300 import build
+    build.build()
+    return torch
+
+
+def _pot(wl):
+    pot = P.Potential(wl.desc, wl.archs)
+    P.panna_set_qeq(pot.ctx, wl.qeq["sigma"], wl.qeq["chi0"], wl.qeq["hard0"])
+    return pot
+
+
+def _compare(torch, wl, charge):
+    pot = _pot(wl)
+    sysd = P.DeviceSystem(wl.system)
+    th32 = wl.theta.astype(np.float32)
+    Q = None if charge is None else torch.as_tensor(charge, dtype=torch.float64, device="cuda")
+    E, Ea, q, F = pot.qeq_energy_forces(sysd, torch.as_tensor(th32, device="cuda"), Q)
+    ref = O.qeq_batch(wl.system, wl.desc, wl.archs, th32.astype(np.float64), wl.qeq, charge)
+    escale = max(np.abs(ref["E_atom"]).sum(), 1e-30)
+    errs = dict(
+        E=float(np.abs(E.cpu().numpy() - ref["E_cfg"]).max() / escale),
+        E_atom=float(np.abs(Ea.cpu().numpy() - ref["E_atom"]).max() / max(np.abs(ref["E_atom"]).max(), 1e-30)),
+        q=float(np.abs(q.cpu().numpy() - ref["q"]).max()),
+        F=H.force_error(F.cpu().numpy().astype(np.float64), ref["F"])[0])
+    return errs, (E, Ea, q, F), ref
+
+
+def test_qeq_clusters_match_oracle(torch_cuda):
+    wl = W.make("nacl64")
+    errs, out, ref = _compare(torch_cuda, wl, wl.charge)
+    q = out[2].cpu().numpy()
+    sums = np.add.reduceat(q, wl.system.atom_off[:-1])
+    print("nacl64 (%d atoms): %s; total charges %.3g..%.3g" % (wl.system.n_atoms, errs, sums.min(), sums.max()))
+    assert np.abs(sums - 1.0).max() <= 1e-9
+    assert errs["E"] <= H.TOL_E and errs["E_atom"] <= 1e-5 and errs["q"] <= 1e-5 and errs["F"] <= H.TOL_F_FP32
+
+
+def test_qeq_total_charges_and_neutral_default(torch_cuda):
+    wl = W.make("nacl64")
+    charge = np.array([(-1.0) ** c * (c % 3) for c in range(wl.system.n_cfg)])
+    errs, out, _ = _compare(torch_cuda, wl, charge)
+    print("per-configuration charges: %s" % errs)
+    assert errs["E"] <= H.TOL_E and errs["q"] <= 1e-5 and errs["F"] <= H.TOL_F_FP32
+    errs0, out0, _ = _compare(torch_cuda, wl, None)
+    print("neutral: %s" % errs0)
+    assert errs0["E"] <= H.TOL_E and errs0["q"] <= 1e-5 and errs0["F"] <= H.TOL_F_FP32
+    sums = np.add.reduceat(out0[2].cpu().numpy(), wl.system.atom_off[:-1])
+    assert np.abs(sums).max() <= 1e-9
+
+
+def _with_edges(wl):
+    s = wl.system
+    parts = [(s.pos[:17], s.species[:17]), (np.zeros((0, 3)), np.zeros(0, np.int32)),
+             (np.array([[1.0, 2.0, 3.0]]), np.array([1], np.int32)),
+             (np.array([[0.0, 0.0, 0.0], [2.6, 0.3, -0.2]]), np.array([0, 1], np.int32)),
+             (s.pos[17:33], s.species[17:33])]
+    off = np.concatenate([[0], np.cumsum([len(p[1]) for p in parts])]).astype(np.int64)
+    C = len(parts)
+    wl.system = W.System(off, np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+                         np.zeros((C, 9)), np.zeros((C, 3), np.uint8), 2)
+    return wl, np.array([1.0, 0.0, 0.5, 0.0, 1.0])
+
+
+def test_qeq_edge_cases(torch_cuda):
+    wl, charge = _with_edges(W.make("nacl2"))
+    errs, out, ref = _compare(torch_cuda, wl, charge)
+    q = out[2].cpu().numpy()
+    print("empty / lone atom / dimer between clusters: %s; lone-atom charge %.6f" % (errs, q[17]))
+    assert abs(q[17] - 0.5) <= 1e-12 and out[0][1].item() == 0.0
+    assert errs["E"] <= H.TOL_E and errs["q"] <= 1e-5 and errs["F"] <= H.TOL_F_FP32
+
+
+def test_qeq_repeat_calls_agree(torch_cuda):
+    torch = torch_cuda
+    wl = W.make("nacl64")
+    pot = _pot(wl)
+    sysd = P.DeviceSystem(wl.system)
+    theta = torch.as_tensor(wl.theta.astype(np.float32), device="cuda")
+    Q = torch.as_tensor(wl.charge, device="cuda")
+    a = pot.qeq_energy_forces(sysd, theta, Q)
+    b = pot.qeq_energy_forces(sysd, theta, Q)
+    # (the flattened descriptor kernels sum in shared memory: equal up to rounding)
+    assert (a[2] - b[2]).abs().max().item() <= 1e-6 and (a[1] - b[1]).abs().max().item() <= 1e-6 * a[1].abs().max().item()
+    assert (a[3] - b[3]).abs().max().item() <= 1e-6 * a[3].abs().max().item()
+
+
+def test_qeq_arguments(torch_cuda):
+    torch = torch_cuda
+    wl = W.make("nacl2")
+    theta = torch.as_tensor(wl.theta.astype(np.float32), device="cuda")
+    pot = P.Potential(wl.desc, wl.archs)
+    sysd = P.DeviceSystem(wl.system)
+    E = torch.empty(2, dtype=torch.float64, device="cuda")
+    F = torch.empty((wl.system.n_atoms, 3), dtype=torch.float32, device="cuda")
+    # constants not set yet
+    with pytest.raises(P.PannaError) as ei:
+        P.panna_qeq_energy_forces(pot.ctx, sysd, theta, None, E, None, None, F)
+    assert ei.value.status == P.PANNA_ERR_INVALID_ARG
+    with pytest.raises(P.PannaError) as ei:
+        P.panna_set_qeq(pot.ctx, [0.0, 1.0], [1.0, 1.0], [1.0, 1.0])
+    assert ei.value.status == P.PANNA_ERR_INVALID_ARG
+    P.panna_set_qeq(pot.ctx, wl.qeq["sigma"], wl.qeq["chi0"], wl.qeq["hard0"])
+    # 3-output networks do not serve the energy-only calls
+    with pytest.raises(P.PannaError) as ei:
+        pot.energy_forces(sysd, theta)
+    assert ei.value.status == P.PANNA_ERR_UNSUPPORTED
+    # periodic configurations and oversized ones are rejected
+    s = wl.system
+    per = P.DeviceSystem(W.System(s.atom_off, s.pos, s.species, np.tile((np.eye(3) * 30.0).reshape(1, 9), (2, 1)),
+                                  np.ones((2, 3), np.uint8), 2))
+    with pytest.raises(P.PannaError) as ei:
+        P.panna_qeq_energy_forces(pot.ctx, per, theta, None, E, None, None, F)
+    assert ei.value.status == P.PANNA_ERR_UNSUPPORTED
+    rng = np.random.default_rng(0)
+    big = W.System(np.array([0, 130], np.int64), rng.uniform(0, 30, (130, 3)), rng.integers(0, 2, 130).astype(np.int32),
+                   np.zeros((1, 9)), np.zeros((1, 3), np.uint8), 2)
+    Fb = torch.empty((130, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(P.PannaError) as ei:
+        P.panna_qeq_energy_forces(pot.ctx, P.DeviceSystem(big), theta, None, E[:1], None, None, Fb)
+    assert ei.value.status == P.PANNA_ERR_UNSUPPORTED
+    # a context with single-output networks has no charge equilibration
+    one = W.make("molecules16")
+    pot1 = P.Potential(one.desc, one.archs)
+    with pytest.raises(P.PannaError) as ei:
+        P.panna_set_qeq(pot1.ctx, [1.0] * 4, [1.0] * 4, [1.0] * 4)
+    assert ei.value.status == P.PANNA_ERR_INVALID_ARG
