@@ -390,7 +390,8 @@ panna_status panna_loss_grad(panna_ctx* ctx, const panna_system* sys, const floa
  *     K_ii = k / (sigma_i sqrt(pi)),
  * and the charges q of each configuration are the stationary point of E_c under
  * sum_i q_i = Q_c (the linear system [A 1; 1^T 0][q; lam] = [-chi; Q_c], A = diag(J) + K,
- * solved in FP64 with partial pivoting).  Forces are -dE_c/dx at those charges.  Direct
+ * solved in FP64 with partial pivoting; erf and exp of the pair terms in FP32).  Forces are
+ * -dE_c/dx at those charges.  Direct
  * sums over all pairs of a configuration: non-periodic configurations of at most 128 atoms
  * (clusters, molecules; PANNA_ERR_UNSUPPORTED otherwise).  Units: A, e, eV;
  * k_coulomb = 0 selects 14.399645478425668 eV A / e^2.

@@ -25,13 +25,17 @@ namespace panna {
 
 constexpr int kQeqThreads = 128;
 
-// Gaussian-charge pair interaction and its derivative with respect to r
+// Gaussian-charge pair interaction and its derivative with respect to r.  erf and exp run
+// in single precision (relative error ~1e-7, far inside the FP32 force tolerance): FP64
+// transcendentals on the GB300's narrow FP64 pipe made the solve the slowest stage.
 __device__ __forceinline__ void qeq_pair(double r, double si, double sj, double ke, double& K, double& dK)
 {
     const double g = sqrt(2.0 * (si * si + sj * sj));
-    const double e = erf(r / g);
+    const float t = (float)(r / g);
+    const double e = (double)erff(t);
+    const double x = (double)expf(-t * t);
     K = ke * e / r;
-    dK = ke * (M_2_SQRTPI * exp(-(r / g) * (r / g)) / (g * r) - e / (r * r));
+    dK = ke * (M_2_SQRTPI * x / (g * r) - e / (r * r));
 }
 
 __global__ void __launch_bounds__(kQeqThreads)
@@ -69,10 +73,12 @@ k_qeq(QeqDev qp, panna_system sys, const int32_t* __restrict__ row_of_atom, cons
     if (tid == 0) bad = 0;
     __syncthreads();
     const double self = qp.ke / sqrt(M_PI);
+    // upper triangle and diagonal computed, mirrored below the diagonal
     for (int idx = tid; idx < n1 * n1; idx += nt) {
         const int i = idx / n1, j = idx - (idx / n1) * n1;
+        if (j < i) continue;
         double v;
-        if (i < n && j < n) {
+        if (j < n) {
             if (i == j) {
                 v = hd[i] + self / sg[i];
             } else {
@@ -81,9 +87,10 @@ k_qeq(QeqDev qp, panna_system sys, const int32_t* __restrict__ row_of_atom, cons
                 qeq_pair(sqrt(dx * dx + dy * dy + dz * dz), sg[i], sg[j], qp.ke, v, dK);
             }
         } else {
-            v = (i == n && j == n) ? 0.0 : 1.0;
+            v = i == n ? 0.0 : 1.0;
         }
         M[idx] = v;
+        M[j * n1 + i] = v;
     }
     for (int i = tid; i < n1; i += nt) rhs[i] = i < n ? -chi[i] : (Qtot ? Qtot[c] : 0.0);
     __syncthreads();
