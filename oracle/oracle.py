@@ -33,7 +33,8 @@ class OrcDesc(C.Structure):
                 ("n_rad", C.c_int), ("rs_rad", _dp), ("eta_rad", C.c_double),
                 ("n_ang_r", C.c_int), ("rs_ang", _dp),
                 ("n_theta", C.c_int), ("theta_s", _dp),
-                ("eta_ang", C.c_double), ("zeta", C.c_double), ("eps_theta", C.c_double)]
+                ("eta_ang", C.c_double), ("zeta", C.c_double), ("eps_theta", C.c_double),
+                ("angular_kind", C.c_int), ("bp_lambda", _dp), ("bp_zeta", _dp), ("bp_eta", _dp)]
 
 
 class OrcArch(C.Structure):
@@ -109,10 +110,13 @@ class _DescHolder:
         self.rs_rad = np.ascontiguousarray(d.rs_rad, np.float64)
         self.rs_ang = np.ascontiguousarray(d.rs_ang, np.float64)
         self.theta_s = np.ascontiguousarray(d.theta_s, np.float64)
+        bp = getattr(d, "angular", "mbp") == "bp"
+        self.bp = [np.ascontiguousarray(a, np.float64) for a in (d.bp_lambda, d.bp_zeta, d.bp_eta)] if bp else None
         self.s = OrcDesc(int(d.n_species), float(d.rc), len(self.rs_rad), _ptr(self.rs_rad, _dp),
-                         float(d.eta_rad), len(self.rs_ang), _ptr(self.rs_ang, _dp),
-                         len(self.theta_s), _ptr(self.theta_s, _dp), float(d.eta_ang),
-                         float(d.zeta), float(d.eps_theta))
+                         float(d.eta_rad), d.n_ang_r, _ptr(self.rs_ang, _dp),
+                         d.n_theta, _ptr(self.theta_s, _dp), float(d.eta_ang),
+                         float(d.zeta), float(d.eps_theta), 1 if bp else 0,
+                         *([_ptr(a, _dp) for a in self.bp] if bp else [None, None, None]))
 
 
 def _arch(a) -> OrcArch:

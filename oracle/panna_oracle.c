@@ -42,6 +42,10 @@ typedef struct {
     double eta_ang;
     double zeta;
     double eps_theta;
+    int angular_kind;          /* 0: modified angular term (mBP), 1: standard BP term */
+    const double* bp_lambda;   /* [n_theta] BP: lambda_m */
+    const double* bp_zeta;     /* [n_theta] BP: zeta_m */
+    const double* bp_eta;      /* [n_ang_r] BP: eta_n */
 } orc_desc;
 
 /* Network of one species: n_layers, widths[0..n_layers] (widths[0] = D, last = 1),
@@ -228,7 +232,66 @@ void orc_center(const orc_desc* p, int nnb, const double* rv, const int32_t* sp,
         }
     }
 
-    /* angular */
+    if (p->angular_kind == 1) {
+        /*
+         * Standard BP angular term (Behler and Parrinello's G4, the form Sec. II.A cites next
+         * to mBP), block of the unordered species pair {s_j, s_k}, index m*n_ang_r + n,
+         * every unordered pair of distinct neighbour entries j < k counted once:
+         *   G[...] += 2^(1-zeta_m) (1 + lambda_m cos(theta_ijk))^zeta_m   (0 where 1 + lambda cos <= 0)
+         *             exp(-eta_n (r_ij^2 + r_ik^2 + r_jk^2)) f_c(r_ij) f_c(r_ik) f_c(r_jk)
+         * with r_jk = |r_ik - r_ij| (the vectors of the two entries).
+         */
+        for (int e1 = 0; e1 < nnb; ++e1)
+        for (int e2 = e1 + 1; e2 < nnb; ++e2) {
+            const double* a = rv + 3 * e1; const double* b = rv + 3 * e2;
+            double d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+            double ra = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+            double rb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+            double rab = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (!(rab < rc)) continue;
+            double cs = (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) / (ra * rb);
+            double fa = fcut(ra, rc), fb = fcut(rb, rc), fab = fcut(rab, rc);
+            double dfa = dfcut(ra, rc), dfb = dfcut(rb, rc), dfab = dfcut(rab, rc);
+            double F3 = fa * fb * fab;
+            double S2 = ra * ra + rb * rb + rab * rab;
+            double dca[3], dcb[3], dF3a[3], dF3b[3], dSa[3], dSb[3];
+            for (int c = 0; c < 3; ++c) {
+                dca[c] = b[c] / (ra * rb) - cs * a[c] / (ra * ra);
+                dcb[c] = a[c] / (ra * rb) - cs * b[c] / (rb * rb);
+                /* d r_jk / d a = -(b - a)/r_jk, d r_jk / d b = (b - a)/r_jk */
+                dF3a[c] = dfa * a[c] / ra * fb * fab - fa * fb * dfab * d[c] / rab;
+                dF3b[c] = fa * dfb * b[c] / rb * fab + fa * fb * dfab * d[c] / rab;
+                dSa[c] = 2.0 * a[c] - 2.0 * d[c];
+                dSb[c] = 2.0 * b[c] + 2.0 * d[c];
+            }
+            int blk = S * NR + pair_block(sp[e1], sp[e2], S) * NT * NA;
+            for (int m = 0; m < NT; ++m) {
+                double lam = p->bp_lambda[m], zt = p->bp_zeta[m];
+                double base = 1.0 + lam * cs;
+                double A = 0.0, dA = 0.0;   /* A_m and dA_m / dcos */
+                if (base > 0.0) {
+                    A = pow(2.0, 1.0 - zt) * pow(base, zt);
+                    dA = pow(2.0, 1.0 - zt) * zt * lam * pow(base, zt - 1.0);
+                }
+                for (int n = 0; n < NA; ++n) {
+                    double B = exp(-p->bp_eta[n] * S2);
+                    int dd = blk + m * NA + n;
+                    G[dd] += A * B * F3;
+                    if (J) {
+                        for (int c = 0; c < 3; ++c) {
+                            J[(size_t)dd * nnb * 3 + e1 * 3 + c] +=
+                                dA * B * F3 * dca[c] - A * p->bp_eta[n] * B * F3 * dSa[c] + A * B * dF3a[c];
+                            J[(size_t)dd * nnb * 3 + e2 * 3 + c] +=
+                                dA * B * F3 * dcb[c] - A * p->bp_eta[n] * B * F3 * dSb[c] + A * B * dF3b[c];
+                        }
+                    }
+                }
+            }
+        }
+        return;
+    }
+
+    /* angular (mBP) */
     for (int e1 = 0; e1 < nnb; ++e1)
     for (int e2 = e1 + 1; e2 < nnb; ++e2) {
         const double* a = rv + 3 * e1; const double* b = rv + 3 * e2;

@@ -78,7 +78,9 @@ class System:
 
 @dataclasses.dataclass
 class DescriptorParams:
-    """Parameters of the species-resolved radial + angular (mBP-type) descriptor."""
+    """Parameters of the species-resolved radial + angular descriptor: the modified angular
+    term (angular = "mbp": theta_s, rs_ang, eta_ang, zeta) or the standard BP term
+    (angular = "bp": per-sector lambda and zeta, per-shell eta)."""
     n_species: int
     rc: float
     rs_rad: np.ndarray
@@ -88,6 +90,10 @@ class DescriptorParams:
     eta_ang: float
     zeta: float
     eps_theta: float = 1e-6
+    angular: str = "mbp"
+    bp_lambda: Optional[np.ndarray] = None
+    bp_zeta: Optional[np.ndarray] = None
+    bp_eta: Optional[np.ndarray] = None
 
     @property
     def n_rad(self) -> int:
@@ -95,11 +101,11 @@ class DescriptorParams:
 
     @property
     def n_ang_r(self) -> int:
-        return int(len(self.rs_ang))
+        return int(len(self.bp_eta)) if self.angular == "bp" else int(len(self.rs_ang))
 
     @property
     def n_theta(self) -> int:
-        return int(len(self.theta_s))
+        return int(len(self.bp_lambda)) if self.angular == "bp" else int(len(self.theta_s))
 
     @property
     def D(self) -> int:
@@ -533,6 +539,19 @@ GAINS = {
 }
 
 
+def bp_variant(wl: Workload, rad_gain: float, ang_gain: float, lambdas=(1.0, -1.0, 1.0, -1.0),
+               zetas=(1.0, 1.0, 4.0, 4.0), etas=(0.005, 0.05)) -> Workload:
+    """The same configurations with the standard BP angular term (Sec. II.A) in place of the
+    modified one: sectors (lambda_m, zeta_m), shells eta_n (A^-2); networks re-sized to the new D
+    and re-drawn (first-layer angular columns scaled by ang_gain)."""
+    rng = np.random.default_rng(wl.seed + 7)
+    desc = dataclasses.replace(wl.desc, angular="bp", bp_lambda=np.asarray(lambdas, np.float64),
+                               bp_zeta=np.asarray(zetas, np.float64), bp_eta=np.asarray(etas, np.float64))
+    archs = [MLPArch((desc.D,) + tuple(a.widths[1:]), a.acts) for a in wl.archs]
+    theta = init_weights(rng, desc, archs, rad_gain, ang_gain)
+    return dataclasses.replace(wl, name=wl.name + "_bp", desc=desc, archs=archs, theta=theta)
+
+
 def make(name: str, seed: int = 0) -> Workload:
     """Workload by name, including the small variants used by the CPU oracle."""
     table = {
@@ -550,6 +569,9 @@ def make(name: str, seed: int = 0) -> Workload:
         "carbon16": lambda: carbon16(seed),
         "carbon16x64": lambda: carbon16(seed, 64),
         "carbon16x4096": lambda: carbon16(seed, 4096),
+        "molecules16_bp": lambda: bp_variant(molecules(seed, 16), 1.0, 0.3),
+        "molecules1024_bp": lambda: bp_variant(molecules(seed, 1024), 1.0, 0.3),
+        "water512_bp": lambda: bp_variant(water(seed, 512), 1.0, 0.05),
         "nacl2": lambda: nacl(seed, 2),
         "nacl64": lambda: nacl(seed, 64),
         "nacl4096": lambda: nacl(seed, 4096),
