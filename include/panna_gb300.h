@@ -81,6 +81,17 @@ enum { PANNA_MLP_FP32 = 0, PANNA_MLP_BF16 = 1, PANNA_MLP_BF16_FAST = 2 };
  * Size D = S*n_rad + S(S+1)/2 * n_theta * n_ang_r (Sec. III.A, III.B sizes).
  * The forms follow the standard BP / PANNA 1.0 mBP descriptors that Sec. II.A cites.
  */
+/*
+ * angular_kind = PANNA_ANGULAR_BP selects the standard Behler-Parrinello angular term instead
+ * (the other form Sec. II.A names), in the same species-pair block layout, entry m*n_ang_r + n:
+ *     G[...] = sum_{j<k} 2^(1-bp_zeta[m]) max(0, 1 + bp_lambda[m] cos(theta_ijk))^bp_zeta[m]
+ *              exp(-bp_eta[n] (r_ij^2 + r_ik^2 + r_jk^2)) f_c(r_ij) f_c(r_ik) f_c(r_jk)
+ * (n_theta sectors (lambda, zeta), n_ang_r shells eta; rs_ang, theta_s, eta_ang, zeta and
+ * eps_theta are not read).  The BP kernels run in plain FP32 and the pair-block kernel
+ * layout only (the kernel-variant knobs do not apply); stored Jacobians take mBP only.
+ */
+#define PANNA_ANGULAR_MBP 0
+#define PANNA_ANGULAR_BP 1
 typedef struct {
     int32_t n_species;      /* S, 1..8 */
     double rc;              /* cutoff (Angstrom), > 0 */
@@ -94,6 +105,10 @@ typedef struct {
     double eta_ang;         /* >= 0 */
     double zeta;            /* >= 1 */
     double eps_theta;       /* >= 0 */
+    int32_t angular_kind;   /* PANNA_ANGULAR_MBP (0) or PANNA_ANGULAR_BP (1) */
+    const double* bp_lambda;  /* [n_theta] BP: finite */
+    const double* bp_zeta;    /* [n_theta] BP: >= 1 */
+    const double* bp_eta;     /* [n_ang_r] BP: >= 0 (A^-2) */
 } panna_desc_params;
 
 #define PANNA_MAX_LAYERS 8

@@ -597,41 +597,25 @@ panna_status panna_create(const panna_desc_params* p, int32_t n_archs, const pan
     *out = nullptr;
     const int64_t D = desc_size(p);
     if (D < 0) return fail(PANNA_ERR_INVALID_ARG, "invalid descriptor sizes or species count (1..%d)", kMaxSpecies);
-    if (p->n_rad > kMaxRad || p->n_ang_r > kMaxAngR || p->n_theta > kMaxTheta)
-        return fail(PANNA_ERR_UNSUPPORTED, "grid larger than %d radial / %d angular-radial / %d theta", kMaxRad,
-                    kMaxAngR, kMaxTheta);
-    if (!(p->rc > 0.0) || !(p->eta_rad >= 0.0) || !(p->eta_ang >= 0.0) || !(p->zeta >= 1.0) || !(p->eps_theta >= 0.0))
-        return fail(PANNA_ERR_INVALID_ARG, "rc > 0, eta >= 0, zeta >= 1, eps_theta >= 0 required");
-    if (!p->rs_rad || !p->rs_ang || !p->theta_s) return fail(PANNA_ERR_INVALID_ARG, "null parameter grid");
+    bool unsupported = false;
+    if (const char* why = desc_params_check(p, &unsupported))
+        return fail(unsupported ? PANNA_ERR_UNSUPPORTED : PANNA_ERR_INVALID_ARG, "%s", why);
     if (n_archs != p->n_species || !archs) return fail(PANNA_ERR_INVALID_ARG, "one network per species required");
     panna_ctx* c = new panna_ctx();
     cudaGetDevice(&c->device);
     DescDev& d = c->d;
-    d.S = p->n_species; d.n_rad = p->n_rad; d.n_ang_r = p->n_ang_r; d.n_theta = p->n_theta;
-    d.D = (int)D; d.n_blocks = d.S * (d.S + 1) / 2; d.rad_cols = d.S * d.n_rad;
-    d.rc = (float)p->rc; d.rc2 = d.rc * d.rc; d.rc_d = p->rc;
-    d.eta_rad = (float)p->eta_rad; d.eta_ang = (float)p->eta_ang; d.zeta = (float)p->zeta;
-    d.eps_theta = (float)p->eps_theta;
-    d.pi_rc = (float)(M_PI / p->rc);
-    d.zeta_int = (p->zeta == floor(p->zeta) && p->zeta <= 4096.0) ? (int)p->zeta : 0;
-    for (int k = 0; k < p->n_rad; ++k) c->d.rs_rad[k] = (float)p->rs_rad[k];
-    for (int k = 0; k < p->n_ang_r; ++k) c->d.rs_ang[k] = (float)p->rs_ang[k];
-    for (int k = 0; k < p->n_theta; ++k) {
-        const double hc = 0.5 * cos(p->theta_s[k]), hs = 0.5 * sin(p->theta_s[k]);
-        c->d.half_cos_t[k] = (float)hc;
-        c->d.half_sin_t[k] = (float)hs;
-        c->d.half_cos_lo[k] = (float)(hc - (double)(float)hc);
-        c->d.half_sin_lo[k] = (float)(hs - (double)(float)hs);
-    }
-    c->d.eps_theta_lo = (float)(p->eps_theta - (double)(float)p->eps_theta);
+    desc_dev_from_params(p, d);
     DescGrid64& g64 = c->g64;
-    g64.rc = p->rc; g64.eta_rad = p->eta_rad; g64.eta_ang = p->eta_ang; g64.zeta = p->zeta;
-    g64.eps_theta = p->eps_theta; g64.pref = pow(2.0, 1.0 - p->zeta); g64.zeta_int = d.zeta_int;
+    g64.rc = p->rc; g64.eta_rad = p->eta_rad;
     for (int k = 0; k < p->n_rad; ++k) g64.rs_rad[k] = p->rs_rad[k];
-    for (int k = 0; k < p->n_ang_r; ++k) g64.rs_ang[k] = p->rs_ang[k];
-    for (int k = 0; k < p->n_theta; ++k) {
-        g64.cos_t[k] = cos(p->theta_s[k]);
-        g64.sin_t[k] = sin(p->theta_s[k]);
+    if (d.ang_kind == 0) {   // the stored Jacobians take the modified angular term
+        g64.eta_ang = p->eta_ang; g64.zeta = p->zeta;
+        g64.eps_theta = p->eps_theta; g64.pref = pow(2.0, 1.0 - p->zeta); g64.zeta_int = d.zeta_int;
+        for (int k = 0; k < p->n_ang_r; ++k) g64.rs_ang[k] = p->rs_ang[k];
+        for (int k = 0; k < p->n_theta; ++k) {
+            g64.cos_t[k] = cos(p->theta_s[k]);
+            g64.sin_t[k] = sin(p->theta_s[k]);
+        }
     }
     MlpPlan& pl = c->plan;
     pl.S = d.S;
@@ -1104,6 +1088,7 @@ panna_status panna_store_plan(panna_ctx* c, const panna_system* sys, panna_store
     if (!info) return fail(PANNA_ERR_INVALID_ARG, "null info");
     if (sys->ghost) return fail(PANNA_ERR_UNSUPPORTED, "stored descriptors of a batch with ghost atoms");
     if (c->d.D > kStoreMaxD) return fail(PANNA_ERR_UNSUPPORTED, "stored descriptors take D <= %d", kStoreMaxD);
+    if (c->d.ang_kind != 0) return fail(PANNA_ERR_UNSUPPORTED, "stored Jacobians take the modified angular term");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(c->device));
     Layout L;

@@ -43,7 +43,18 @@ struct DescDev {
     float half_cos_lo[kMaxTheta];  // remainders: exact value - float value
     float half_sin_lo[kMaxTheta];
     float eps_theta_lo;
+    // standard BP angular term (ang_kind 1): sector m = (lambda_m, zeta_m), shell n = eta_n
+    int32_t ang_kind;              // 0 = modified (mBP), 1 = standard BP
+    float bp_lambda[kMaxTheta], bp_zeta[kMaxTheta], bp_pref[kMaxTheta];   // pref = 2^(1 - zeta)
+    int32_t bp_zeta_int[kMaxTheta];   // zeta when an integer in [1, 4096], else 0
+    float bp_eta[kMaxAngR];
 };
+
+// Descriptor parameters (descriptor.cu): nullptr when valid, else the reason
+// (*unsupported: a grid beyond the kernels' limits rather than an invalid value); and the
+// DescDev of valid parameters
+const char* desc_params_check(const panna_desc_params* p, bool* unsupported);
+void desc_dev_from_params(const panna_desc_params* p, DescDev& d);
 
 // Geometry of one configuration as binned on the device.
 struct CfgGeom {

@@ -86,11 +86,9 @@ extern "C" panna_status panna_descriptors_static(const panna_desc_params* p, con
 {
     char msg[256];
     if (!p || !sys || !G) return sfail(PANNA_ERR_INVALID_ARG, "null argument");
-    if (p->n_species < 1 || p->n_species > kMaxSpecies || p->n_rad < 1 || p->n_ang_r < 1 || p->n_theta < 1 ||
-        p->n_rad > kMaxRad || p->n_ang_r > kMaxAngR || p->n_theta > kMaxTheta || !p->rs_rad || !p->rs_ang ||
-        !p->theta_s || !(p->rc > 0.0) || !(p->zeta >= 1.0) || !(p->eps_theta >= 0.0) || !(p->eta_rad >= 0.0) ||
-        !(p->eta_ang >= 0.0))
-        return sfail(PANNA_ERR_INVALID_ARG, "invalid descriptor parameters");
+    bool unsupported = false;
+    if (const char* why = desc_params_check(p, &unsupported))
+        return sfail(PANNA_ERR_INVALID_ARG, why);
     const int64_t N = sys->n_atoms, C = sys->n_cfg;
     if (C < 1 || N < 0 || !sys->atom_off || !sys->cell || !sys->pbc || (N > 0 && (!sys->pos || !sys->species)))
         return sfail(PANNA_ERR_INVALID_ARG, "invalid system");
@@ -134,24 +132,7 @@ extern "C" panna_status panna_descriptors_static(const panna_desc_params* p, con
 
     // descriptor parameters as the kernels read them
     DescDev d{};
-    d.S = p->n_species; d.n_rad = p->n_rad; d.n_ang_r = p->n_ang_r; d.n_theta = p->n_theta;
-    d.D = d.S * d.n_rad + d.S * (d.S + 1) / 2 * d.n_theta * d.n_ang_r;
-    d.n_blocks = d.S * (d.S + 1) / 2; d.rad_cols = d.S * d.n_rad;
-    d.rc = (float)p->rc; d.rc2 = d.rc * d.rc; d.rc_d = p->rc;
-    d.eta_rad = (float)p->eta_rad; d.eta_ang = (float)p->eta_ang; d.zeta = (float)p->zeta;
-    d.eps_theta = (float)p->eps_theta;
-    d.eps_theta_lo = (float)(p->eps_theta - (double)(float)p->eps_theta);
-    d.pi_rc = (float)(M_PI / p->rc);
-    d.zeta_int = (p->zeta == floor(p->zeta) && p->zeta <= 4096.0) ? (int)p->zeta : 0;
-    for (int k = 0; k < p->n_rad; ++k) d.rs_rad[k] = (float)p->rs_rad[k];
-    for (int k = 0; k < p->n_ang_r; ++k) d.rs_ang[k] = (float)p->rs_ang[k];
-    for (int k = 0; k < p->n_theta; ++k) {
-        const double hc = 0.5 * cos(p->theta_s[k]), hs = 0.5 * sin(p->theta_s[k]);
-        d.half_cos_t[k] = (float)hc;
-        d.half_sin_t[k] = (float)hs;
-        d.half_cos_lo[k] = (float)(hc - (double)(float)hc);
-        d.half_sin_lo[k] = (float)(hs - (double)(float)hs);
-    }
+    desc_dev_from_params(p, d);
 
     for (int attempt = 0; attempt < 2; ++attempt) {
         carve_static(base, N, C, (int)cap, w);

@@ -33,7 +33,11 @@ class panna_desc_params(C.Structure):
                 ("n_rad", C.c_int32), ("rs_rad", _dp), ("eta_rad", C.c_double),
                 ("n_ang_r", C.c_int32), ("rs_ang", _dp),
                 ("n_theta", C.c_int32), ("theta_s", _dp),
-                ("eta_ang", C.c_double), ("zeta", C.c_double), ("eps_theta", C.c_double)]
+                ("eta_ang", C.c_double), ("zeta", C.c_double), ("eps_theta", C.c_double),
+                ("angular_kind", C.c_int32), ("bp_lambda", _dp), ("bp_zeta", _dp), ("bp_eta", _dp)]
+
+
+PANNA_ANGULAR_MBP, PANNA_ANGULAR_BP = 0, 1
 
 
 class panna_mlp_arch(C.Structure):
@@ -180,10 +184,14 @@ class _DescHolder:
         self.rs_rad = np.ascontiguousarray(d.rs_rad, np.float64)
         self.rs_ang = np.ascontiguousarray(d.rs_ang, np.float64)
         self.theta_s = np.ascontiguousarray(d.theta_s, np.float64)
+        bp = getattr(d, "angular", "mbp") == "bp"
+        self.bp = [np.ascontiguousarray(a, np.float64) for a in (d.bp_lambda, d.bp_zeta, d.bp_eta)] if bp else []
+        bp_ptrs = [a.ctypes.data_as(_dp) for a in self.bp] if bp else [None, None, None]
         self.s = panna_desc_params(
             int(d.n_species), float(d.rc), len(self.rs_rad), self.rs_rad.ctypes.data_as(_dp), float(d.eta_rad),
-            len(self.rs_ang), self.rs_ang.ctypes.data_as(_dp), len(self.theta_s),
-            self.theta_s.ctypes.data_as(_dp), float(d.eta_ang), float(d.zeta), float(d.eps_theta))
+            int(d.n_ang_r), self.rs_ang.ctypes.data_as(_dp), int(d.n_theta),
+            self.theta_s.ctypes.data_as(_dp), float(d.eta_ang), float(d.zeta), float(d.eps_theta),
+            PANNA_ANGULAR_BP if bp else PANNA_ANGULAR_MBP, *bp_ptrs)
 
 
 def panna_descriptor_size(desc) -> int:
