@@ -75,7 +75,10 @@ def test_bp_training_gradient_matches_oracle(torch_cuda, name):
     th64 = wl.theta.astype(np.float32).astype(np.float64)
     base = O.batch(wl.system, wl.desc, wl.archs, th64)
     rng = np.random.default_rng(2)
-    e_ref = base["E_cfg"] + rng.normal(0.0, 0.3, size=wl.system.n_cfg)
+    # labels off by O(1) per atom (as the other training tests): the energy residual of a
+    # 512-atom box then dwarfs the FP32 rounding of its 512-term sum
+    n = np.diff(wl.system.atom_off)
+    e_ref = base["E_cfg"] + rng.normal(0.0, 0.2, size=wl.system.n_cfg) * n
     f_ref = (base["F"] + rng.normal(0.0, 0.3, size=base["F"].shape)).astype(np.float32).astype(np.float64)
     loss, g, E, F = pot.loss_grad(P.DeviceSystem(wl.system), torch.as_tensor(th64.astype(np.float32), device="cuda"),
                                   torch.as_tensor(e_ref, device="cuda"),
