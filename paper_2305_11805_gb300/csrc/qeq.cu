@@ -25,162 +25,176 @@ namespace panna {
 
 constexpr int kQeqThreads = 128;
 
-// Gaussian-charge pair interaction and its derivative with respect to r.  erf and exp run
-// in single precision (relative error ~1e-7, far inside the FP32 force tolerance): FP64
-// transcendentals on the GB300's narrow FP64 pipe made the solve the slowest stage.
-__device__ __forceinline__ void qeq_pair(double r, double si, double sj, double ke, double& K, double& dK)
+// Gaussian-charge pair interaction and its derivative with respect to r, in single
+// precision (relative error ~1e-7, far inside the FP32 force tolerance; the matrix, the
+// solve and every sum stay FP64): FP64 square roots, divisions and transcendentals on the
+// GB300's narrow FP64 pipe made this the slowest part of the call.
+__device__ __forceinline__ void qeq_pair(float r, float si, float sj, float ke, float& K, float& dK)
 {
-    const double g = sqrt(2.0 * (si * si + sj * sj));
-    const float t = (float)(r / g);
-    const double e = (double)erff(t);
-    const double x = (double)expf(-t * t);
-    K = ke * e / r;
-    dK = ke * (M_2_SQRTPI * x / (g * r) - e / (r * r));
+    const float ig = rsqrtf(2.f * (si * si + sj * sj));
+    const float t = r * ig;
+    const float e = erff(t);
+    const float ir = 1.f / r;
+    K = ke * e * ir;
+    dK = ke * ir * (1.1283791670955126f * __expf(-t * t) * ig - e * ir);
+}
+
+// distance of two staged atoms (FP64 positions, difference rounded to FP32)
+__device__ __forceinline__ float qeq_dist(const double* px, const double* py, const double* pz, int i, int j,
+                                          float& dx, float& dy, float& dz)
+{
+    dx = (float)(px[i] - px[j]);
+    dy = (float)(py[i] - py[j]);
+    dz = (float)(pz[i] - pz[j]);
+    return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
 }
 
 __global__ void __launch_bounds__(kQeqThreads)
-k_qeq(QeqDev qp, panna_system sys, const int32_t* __restrict__ row_of_atom, const float* __restrict__ out,
+k_qeq(QeqDev qp, panna_system sys, int64_t C, const int32_t* __restrict__ row_of_atom, const float* __restrict__ out,
       int ldo, const double* __restrict__ Qtot, float* __restrict__ E_rows, double* __restrict__ charges,
       float* __restrict__ F, float* __restrict__ seeds, int lds, DevStatus* status, int n_lo, int n_hi)
 {
     extern __shared__ double sm[];
     __shared__ int piv, bad;
-    const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-    const int64_t a0 = sys.atom_off[c];
-    const int64_t n64 = sys.atom_off[c + 1] - a0;
-    if (n64 <= n_lo || (n64 > n_hi && n_hi < kQeqMax)) return;   // another size class
-    const int n = (int)(n64 > kQeqMax ? kQeqMax + 1 : n64);
-    if (n > kQeqMax || sys.pbc[3 * c] || sys.pbc[3 * c + 1] || sys.pbc[3 * c + 2]) {
-        if (tid == 0) set_status(status, PANNA_ERR_UNSUPPORTED, c);
-        return;
-    }
-    const int n1 = n + 1;
-    double* M = sm;
-    double* rhs = M + n1 * n1;
-    double* x = rhs + n1;
-    double* px = x + n1; double* py = px + n; double* pz = py + n;
-    double* sg = pz + n; double* chi = sg + n; double* hd = chi + n; double* ee = hd + n;
-    for (int i = tid; i < n; i += nt) {
-        const int64_t a = a0 + i;
-        const int64_t r = row_of_atom[a];
-        const int s = sys.species[a];
-        px[i] = sys.pos[3 * a]; py[i] = sys.pos[3 * a + 1]; pz[i] = sys.pos[3 * a + 2];
-        sg[i] = qp.sigma[s];
-        ee[i] = out[r * ldo];
-        chi[i] = qp.chi0[s] + out[r * ldo + 1];
-        hd[i] = qp.hard0[s] + out[r * ldo + 2];
-    }
-    if (tid == 0) bad = 0;
-    __syncthreads();
-    const double self = qp.ke / sqrt(M_PI);
-    // upper triangle and diagonal computed, mirrored below the diagonal
-    for (int idx = tid; idx < n1 * n1; idx += nt) {
-        const int i = idx / n1, j = idx - (idx / n1) * n1;
-        if (j < i) continue;
-        double v;
-        if (j < n) {
-            if (i == j) {
-                v = hd[i] + self / sg[i];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int64_t c = blockIdx.x; c < C; c += gridDim.x) {
+        const int64_t a0 = sys.atom_off[c];
+        const int64_t n64 = sys.atom_off[c + 1] - a0;
+        if (n64 <= n_lo || (n64 > n_hi && n_hi < kQeqMax)) continue;   // another size class
+        const int n = (int)(n64 > kQeqMax ? kQeqMax + 1 : n64);
+        if (n > kQeqMax || sys.pbc[3 * c] || sys.pbc[3 * c + 1] || sys.pbc[3 * c + 2]) {
+            if (tid == 0) set_status(status, PANNA_ERR_UNSUPPORTED, (int)c);
+            continue;
+        }
+        __syncthreads();   // the previous configuration's shared data is no longer read
+        const int n1 = n + 1;
+        double* M = sm;
+        double* rhs = M + n1 * n1;
+        double* x = rhs + n1;
+        double* px = x + n1; double* py = px + n; double* pz = py + n;
+        double* sg = pz + n; double* chi = sg + n; double* hd = chi + n; double* ee = hd + n;
+        for (int i = tid; i < n; i += nt) {
+            const int64_t a = a0 + i;
+            const int64_t r = row_of_atom[a];
+            const int s = sys.species[a];
+            px[i] = sys.pos[3 * a]; py[i] = sys.pos[3 * a + 1]; pz[i] = sys.pos[3 * a + 2];
+            sg[i] = qp.sigma[s];
+            ee[i] = out[r * ldo];
+            chi[i] = qp.chi0[s] + out[r * ldo + 1];
+            hd[i] = qp.hard0[s] + out[r * ldo + 2];
+        }
+        if (tid == 0) bad = 0;
+        __syncthreads();
+        const double self = qp.ke / sqrt(M_PI);
+        // upper triangle and diagonal computed, mirrored below the diagonal
+        for (int idx = tid; idx < n1 * n1; idx += nt) {
+            const int i = idx / n1, j = idx - (idx / n1) * n1;
+            if (j < i) continue;
+            double v;
+            if (j < n) {
+                if (i == j) {
+                    v = hd[i] + self / sg[i];
+                } else {
+                    float dx, dy, dz, K, dK;
+                    qeq_pair(qeq_dist(px, py, pz, i, j, dx, dy, dz), (float)sg[i], (float)sg[j], (float)qp.ke, K, dK);
+                    v = K;
+                }
             } else {
-                const double dx = px[i] - px[j], dy = py[i] - py[j], dz = pz[i] - pz[j];
-                double dK;
-                qeq_pair(sqrt(dx * dx + dy * dy + dz * dz), sg[i], sg[j], qp.ke, v, dK);
+                v = i == n ? 0.0 : 1.0;
             }
-        } else {
-            v = i == n ? 0.0 : 1.0;
+            M[idx] = v;
+            M[j * n1 + i] = v;
         }
-        M[idx] = v;
-        M[j * n1 + i] = v;
-    }
-    for (int i = tid; i < n1; i += nt) rhs[i] = i < n ? -chi[i] : (Qtot ? Qtot[c] : 0.0);
-    __syncthreads();
+        for (int i = tid; i < n1; i += nt) rhs[i] = i < n ? -chi[i] : (Qtot ? Qtot[c] : 0.0);
+        __syncthreads();
 
-    // elimination with partial pivoting
-    for (int k = 0; k < n1; ++k) {
+        // elimination with partial pivoting
+        for (int k = 0; k < n1; ++k) {
+            if (tid < 32) {
+                double best = -1.0;
+                int bi = k;
+                for (int i = k + tid; i < n1; i += 32) {
+                    const double a = fabs(M[i * n1 + k]);
+                    if (a > best) { best = a; bi = i; }
+                }
+    #pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                }
+                if (tid == 0) {
+                    piv = bi;
+                    if (!(best > 0.0) || !isfinite(best)) bad = 1;
+                }
+            }
+            __syncthreads();
+            if (bad) break;
+            const int p = piv;
+            if (p != k) {
+                for (int j = k + tid; j < n1; j += nt) {
+                    const double t = M[k * n1 + j];
+                    M[k * n1 + j] = M[p * n1 + j];
+                    M[p * n1 + j] = t;
+                }
+                if (tid == 0) {
+                    const double t = rhs[k];
+                    rhs[k] = rhs[p];
+                    rhs[p] = t;
+                }
+            }
+            __syncthreads();
+            const double inv = 1.0 / M[k * n1 + k];
+            const int m = n1 - k - 1;
+            for (int idx = tid; idx < m * m; idx += nt) {
+                const int i = k + 1 + idx / m, j = k + 1 + (idx - (idx / m) * m);
+                M[i * n1 + j] -= M[i * n1 + k] * inv * M[k * n1 + j];
+            }
+            for (int i = k + 1 + tid; i < n1; i += nt) rhs[i] -= M[i * n1 + k] * inv * rhs[k];
+            __syncthreads();
+        }
+        if (bad) {
+            if (tid == 0) set_status(status, PANNA_ERR_BAD_INPUT, (int)c);
+            continue;
+        }
+        // back substitution (one warp)
         if (tid < 32) {
-            double best = -1.0;
-            int bi = k;
-            for (int i = k + tid; i < n1; i += 32) {
-                const double a = fabs(M[i * n1 + k]);
-                if (a > best) { best = a; bi = i; }
-            }
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (tid == 0) {
-                piv = bi;
-                if (!(best > 0.0) || !isfinite(best)) bad = 1;
+            for (int k = n1 - 1; k >= 0; --k) {
+                double acc = 0.0;
+                for (int j = k + 1 + tid; j < n1; j += 32) acc += M[k * n1 + j] * x[j];
+    #pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (tid == 0) x[k] = (rhs[k] - acc) / M[k * n1 + k];
+                __syncwarp();
             }
         }
         __syncthreads();
-        if (bad) break;
-        const int p = piv;
-        if (p != k) {
-            for (int j = k + tid; j < n1; j += nt) {
-                const double t = M[k * n1 + j];
-                M[k * n1 + j] = M[p * n1 + j];
-                M[p * n1 + j] = t;
-            }
-            if (tid == 0) {
-                const double t = rhs[k];
-                rhs[k] = rhs[p];
-                rhs[p] = t;
-            }
-        }
-        __syncthreads();
-        const double inv = 1.0 / M[k * n1 + k];
-        const int m = n1 - k - 1;
-        for (int idx = tid; idx < m * m; idx += nt) {
-            const int i = k + 1 + idx / m, j = k + 1 + (idx - (idx / m) * m);
-            M[i * n1 + j] -= M[i * n1 + k] * inv * M[k * n1 + j];
-        }
-        for (int i = k + 1 + tid; i < n1; i += nt) rhs[i] -= M[i * n1 + k] * inv * rhs[k];
-        __syncthreads();
-    }
-    if (bad) {
-        if (tid == 0) set_status(status, PANNA_ERR_BAD_INPUT, c);
-        return;
-    }
-    // back substitution (one warp)
-    if (tid < 32) {
-        for (int k = n1 - 1; k >= 0; --k) {
-            double acc = 0.0;
-            for (int j = k + 1 + tid; j < n1; j += 32) acc += M[k * n1 + j] * x[j];
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (tid == 0) x[k] = (rhs[k] - acc) / M[k * n1 + k];
-            __syncwarp();
-        }
-    }
-    __syncthreads();
 
-    // energies, pair forces, network seeds
-    for (int i = tid; i < n; i += nt) {
-        const double qi = x[i];
-        double kq = self / sg[i] * qi, fx = 0.0, fy = 0.0, fz = 0.0;
-        for (int j = 0; j < n; ++j) {
-            if (j == i) continue;
-            const double dx = px[i] - px[j], dy = py[i] - py[j], dz = pz[i] - pz[j];
-            const double r = sqrt(dx * dx + dy * dy + dz * dz);
-            double K, dK;
-            qeq_pair(r, sg[i], sg[j], qp.ke, K, dK);
-            kq += K * x[j];
-            const double f = -qi * x[j] * dK / r;
-            fx += f * dx; fy += f * dy; fz += f * dz;
+        // energies, pair forces, network seeds
+        for (int i = tid; i < n; i += nt) {
+            const double qi = x[i];
+            double kq = self / sg[i] * qi, fx = 0.0, fy = 0.0, fz = 0.0;
+            const float si = (float)sg[i], ke = (float)qp.ke;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                float dx, dy, dz, K, dK;
+                const float r = qeq_dist(px, py, pz, i, j, dx, dy, dz);
+                qeq_pair(r, si, (float)sg[j], ke, K, dK);
+                kq += (double)K * x[j];
+                const double f = -qi * x[j] * (double)(dK / r);
+                fx += f * dx; fy += f * dy; fz += f * dz;
+            }
+            const int64_t a = a0 + i;
+            const int64_t r = row_of_atom[a];
+            E_rows[r] = (float)(ee[i] + chi[i] * qi + 0.5 * hd[i] * qi * qi + 0.5 * qi * kq);
+            if (charges) charges[a] = qi;
+            F[3 * a] += (float)fx;
+            F[3 * a + 1] += (float)fy;
+            F[3 * a + 2] += (float)fz;
+            seeds[r * lds] = 1.f;
+            seeds[r * lds + 1] = (float)qi;
+            seeds[r * lds + 2] = (float)(0.5 * qi * qi);
         }
-        const int64_t a = a0 + i;
-        const int64_t r = row_of_atom[a];
-        E_rows[r] = (float)(ee[i] + chi[i] * qi + 0.5 * hd[i] * qi * qi + 0.5 * qi * kq);
-        if (charges) charges[a] = qi;
-        F[3 * a] += (float)fx;
-        F[3 * a + 1] += (float)fy;
-        F[3 * a + 2] += (float)fz;
-        seeds[r * lds] = 1.f;
-        seeds[r * lds + 1] = (float)qi;
-        seeds[r * lds + 2] = (float)(0.5 * qi * qi);
     }
 }
 
@@ -199,11 +213,19 @@ cudaError_t launch_qeq(const QeqDev& qp, const Work& w, const float* out, int ld
     cudaError_t e = cudaFuncSetAttribute(k_qeq, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)qeq_smem_bytes(kQeqMax));
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int k = 0; k < 2; ++k) {
-        // the last class also reports configurations beyond kQeqMax
-        k_qeq<<<(unsigned)w.C, kQeqThreads, qeq_smem_bytes(classes[k + 1]), s>>>(
-            qp, *w.sys, w.row_of_atom, out, ldo, Qtot, E_rows, charges, F, seeds, lds, w.status, classes[k],
-            classes[k + 1]);
+        // resident CTAs of the class, each looping over the configurations; the last class
+        // also reports configurations beyond kQeqMax
+        const size_t smem = qeq_smem_bytes(classes[k + 1]);
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qeq, kQeqThreads, smem);
+        int64_t nb = (int64_t)(sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+        if (nb > w.C) nb = w.C;
+        k_qeq<<<(unsigned)nb, kQeqThreads, smem, s>>>(qp, *w.sys, w.C, w.row_of_atom, out, ldo, Qtot, E_rows,
+                                                      charges, F, seeds, lds, w.status, classes[k], classes[k + 1]);
         ++*launches;
     }
     return cudaGetLastError();
