@@ -482,3 +482,117 @@ def qeq_batch(system, desc, archs, theta, qeq, charge=None, ke=KE_EV_A):
     np.add.at(F, jac["j"], -qe)
     E_cfg = np.array([E_atom[int(s.atom_off[c]):int(s.atom_off[c + 1])].sum() for c in range(s.n_cfg)])
     return dict(E_cfg=E_cfg, E_atom=E_atom, q=q, F=F, lam=lam, chi=chi, hard=hard, out=out3)
+
+
+def mlp_rows_train(arch, theta_s, X, Xdot, seeds, tseeds):
+    """Eq. 1 on rows with a forward tangent along Xdot: returns (outputs, output tangents,
+    dtheta) where dtheta = d/dtheta sum_rows [seeds . out + tseeds . outdot] (the reverse pass
+    over the forward and tangent computations, as orc_mlp does for one output)."""
+    X = np.atleast_2d(np.asarray(X, np.float64))
+    Xd = np.atleast_2d(np.asarray(Xdot, np.float64))
+    Ws, bs, offs, o = [], [], [], 0
+    for l in range(arch.n_layers):
+        fi, fo = arch.widths[l], arch.widths[l + 1]
+        offs.append(o)
+        Ws.append(np.asarray(theta_s[o:o + fo * fi]).reshape(fo, fi))
+        o += fo * fi
+        bs.append(np.asarray(theta_s[o:o + fo]))
+        o += fo
+    a, ad, As, Ads, Zs, Zds = X, Xd, [X], [Xd], [], []
+    for l in range(arch.n_layers):
+        z = a @ Ws[l].T + bs[l]
+        zd = ad @ Ws[l].T
+        t = arch.acts[l]
+        a, ad = _act(t, z), _act_d1(t, z) * zd
+        Zs.append(z); Zds.append(zd); As.append(a); Ads.append(ad)
+    dth = np.zeros(o)
+    bar = np.asarray(seeds, np.float64)
+    bard = np.asarray(tseeds, np.float64)
+    for l in range(arch.n_layers - 1, -1, -1):
+        t, z, zd = arch.acts[l], Zs[l], Zds[l]
+        d1 = _act_d1(t, z)
+        if t == 1:
+            d2 = (4.0 * z * z - 2.0) * np.exp(-z * z)
+        elif t == 3:
+            th = np.tanh(z)
+            d2 = -2.0 * th * (1.0 - th * th)
+        else:
+            d2 = np.zeros_like(z)
+        zb = bar * d1 + bard * d2 * zd
+        zdb = bard * d1
+        fo, fi = Ws[l].shape
+        dth[offs[l]:offs[l] + fo * fi] += (zb.T @ As[l] + zdb.T @ Ads[l]).ravel()
+        dth[offs[l] + fo * fi:offs[l] + fo * fi + fo] += zb.sum(0)
+        bar = zb @ Ws[l]
+        bard = zdb @ Ws[l]
+    return As[-1], Ads[-1], dth
+
+
+def qeq_loss_grad(system, desc, archs, theta, qeq, charge, e_ref, f_ref, w_force, q_ref=None, w_charge=0.0,
+                  ke=KE_EV_A):
+    """Training through the charge layer: loss
+        L = (1/C) sum_c (E_c - E_ref_c)^2 + w_F/(3N) sum (F - F_ref)^2 + w_q sum_i (q_i - q_ref_i)^2
+    (the charge term only with q_ref) and dL/dtheta, by the chain rule in the order of the
+    definition: dE_c/dtheta and the force term's derivative at fixed charges, plus the charges'
+    response dq/dtheta from differentiating the constrained stationarity (one more solve with
+    the same symmetric matrix)."""
+    s = system
+    base = qeq_batch(system, desc, archs, theta, qeq, charge, ke)
+    N, C = s.n_atoms, s.n_cfg
+    q, chi, hard, E_cfg, F = base["q"], base["chi"], base["hard"], base["E_cfg"], base["F"]
+    dE = E_cfg - e_ref
+    dF = F - f_ref
+    loss = (dE ** 2).sum() / C + w_force / (3 * N) * (dF ** 2).sum()
+    if q_ref is not None:
+        loss += w_charge * ((q - q_ref) ** 2).sum()
+    alpha = 2 * dE / C
+    u = 2 * w_force / (3 * N) * dF
+    # descriptor tangent along u: w_i = sum_e J_e (u_j(e) - u_i)
+    G = batch(s, desc, archs, theta, want_G=True)["G"]
+    jac = jacobians(s, desc)
+    w = np.zeros_like(G)
+    np.add.at(w, jac["i"], np.einsum("edc,ec->ed", jac["J"], u[jac["j"]] - u[jac["i"]]))
+    toff = _theta_off(archs)
+    cfg = np.searchsorted(s.atom_off, np.arange(N), side="right") - 1
+    sq = np.stack([np.ones(N), q, 0.5 * q ** 2], 1)
+    # output tangents (network part of u . d(dE/dq)/dx)
+    odot = np.zeros((N, 3))
+    for sp in range(len(archs)):
+        rows = np.nonzero(s.species == sp)[0]
+        if len(rows):
+            odot[rows] = mlp_rows_train(archs[sp], theta[toff[sp]:toff[sp + 1]], G[rows], w[rows],
+                                        np.zeros((len(rows), 3)), np.zeros((len(rows), 3)))[1]
+    sig = np.asarray(qeq["sigma"])[s.species]
+    mu = np.zeros(N)
+    for c in range(C):
+        a0, a1 = int(s.atom_off[c]), int(s.atom_off[c + 1])
+        if a1 == a0:
+            continue
+        n = a1 - a0
+        # v_i = sum_m u_m d/dx_m (dE/dq_i) at fixed charges
+        v = odot[a0:a1, 1] + q[a0:a1] * odot[a0:a1, 2]
+        for i in range(a0, a1):
+            for j in range(a0, a1):
+                if i != j:
+                    d = s.pos[i] - s.pos[j]
+                    r = np.linalg.norm(d)
+                    v[i - a0] += q[j] * qeq_kernel(r, sig[i], sig[j], ke)[1] * d @ (u[i] - u[j]) / r
+        h = -v
+        if q_ref is not None:
+            h = h + 2 * w_charge * (q[a0:a1] - q_ref[a0:a1])
+        _, _, K = qeq_solve(s.pos[a0:a1], sig[a0:a1], chi[a0:a1], hard[a0:a1], 0.0, ke)
+        M = np.zeros((n + 1, n + 1))
+        M[:n, :n] = K + np.diag(hard[a0:a1])
+        M[:n, n] = 1.0
+        M[n, :n] = 1.0
+        mu[a0:a1] = np.linalg.solve(M, np.concatenate([h, [0.0]]))[:n]
+    seeds = alpha[cfg][:, None] * sq
+    seeds[:, 1] -= mu
+    seeds[:, 2] -= mu * q
+    dth = np.zeros(len(theta))
+    for sp in range(len(archs)):
+        rows = np.nonzero(s.species == sp)[0]
+        if len(rows):
+            dth[toff[sp]:toff[sp + 1]] = mlp_rows_train(archs[sp], theta[toff[sp]:toff[sp + 1]], G[rows], w[rows],
+                                                        seeds[rows], -sq[rows])[2]
+    return dict(loss=loss, dtheta=dth, E_cfg=E_cfg, F=F, q=q, mu=mu)

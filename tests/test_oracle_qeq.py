@@ -114,3 +114,68 @@ def test_rotation_and_permutation_invariance():
     np.testing.assert_allclose(out["E_cfg"], ref["E_cfg"], rtol=1e-11)
     np.testing.assert_allclose(out["q"], ref["q"][perm], atol=1e-11)
     np.testing.assert_allclose(out["F"], (ref["F"] @ q_rot.T)[perm], atol=1e-10 * np.abs(ref["F"]).max())
+
+
+def test_mlp_rows_train_matches_single_output_oracle():
+    wl = W.make("nacl2")
+    arch = wl.archs[0]
+    off = W.param_offsets(wl.archs)
+    th = wl.theta[off[0]:off[1]]
+    rng = np.random.default_rng(5)
+    X, Xd = rng.normal(size=(3, arch.widths[0])), rng.normal(size=(3, arch.widths[0]))
+    last = sum(arch.widths[l + 1] * arch.widths[l] + arch.widths[l + 1] for l in range(arch.n_layers - 1))
+    h = arch.widths[-2]
+    one = W.MLPArch(arch.widths[:-1] + (1,), arch.acts)
+    for k in range(3):
+        seeds, tseeds = np.zeros((3, 3)), np.zeros((3, 3))
+        seeds[:, k], tseeds[:, k] = 0.7, -1.3
+        _, _, dth = O.mlp_rows_train(arch, th, X, Xd, seeds, tseeds)
+        want = np.zeros(len(th))
+        for r in range(3):
+            thk = np.concatenate([th[:last], th[last + k * h:last + (k + 1) * h],
+                                  th[last + 3 * h + k:last + 3 * h + k + 1]])
+            _, _, d1 = O.mlp(one, thk, X[r], Xd[r], 0.7, -1.3, param_grad=True)
+            want[:last] += d1[:last]
+            want[last + k * h:last + (k + 1) * h] += d1[last:last + h]
+            want[last + 3 * h + k] += d1[last + h]
+        np.testing.assert_allclose(dth, want, rtol=1e-10, atol=1e-12 * np.abs(want).max())
+
+
+def test_qeq_loss_gradient_central_differences():
+    """Energy, force and charge terms together; the charges' response (the second solve) is a
+    sizeable part of the gradient, so dropping it fails the comparison."""
+    wl = W.make("nacl2")
+    s = wl.system
+    base = O.qeq_batch(s, wl.desc, wl.archs, wl.theta, wl.qeq, wl.charge)
+    rng = np.random.default_rng(0)
+    e_ref = base["E_cfg"] + rng.normal(0, 0.5, 2)
+    f_ref = base["F"] + rng.normal(0, 0.2, base["F"].shape)
+    q_ref = base["q"] + rng.normal(0, 0.05, s.n_atoms)
+    args = (wl.qeq, wl.charge, e_ref, f_ref, 0.7, q_ref, 0.3)
+    r = O.qeq_loss_grad(s, wl.desc, wl.archs, wl.theta, *args)
+    off = W.param_offsets(wl.archs)
+    arch = wl.archs[0]
+    last = sum(arch.widths[l + 1] * arch.widths[l] + arch.widths[l + 1] for l in range(arch.n_layers - 1))
+    picks = list(rng.choice(len(wl.theta), 10, replace=False))
+    # the chi and J output rows of species 0 and 1 (where the charge response enters)
+    picks += [off[0] + last + 15 + 3, off[0] + last + 30 + 4, off[1] + last + 15 + 1, off[1] + last + 30 + 7]
+    h = 1e-6
+    scale = np.abs(r["dtheta"]).max()
+    for k in picks:
+        tp, tm = wl.theta.copy(), wl.theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (O.qeq_loss_grad(s, wl.desc, wl.archs, tp, *args)["loss"] -
+              O.qeq_loss_grad(s, wl.desc, wl.archs, tm, *args)["loss"]) / (2 * h)
+        assert abs(fd - r["dtheta"][k]) <= 1e-6 * scale + 1e-5 * abs(fd), (k, fd, r["dtheta"][k])
+    assert np.abs(r["mu"]).max() > 1e-3
+
+
+def test_qeq_loss_without_labels_terms():
+    """With labels equal to the predictions, only the charge term remains (and vanishes with it)."""
+    wl = W.make("nacl2")
+    s = wl.system
+    base = O.qeq_batch(s, wl.desc, wl.archs, wl.theta, wl.qeq, wl.charge)
+    r = O.qeq_loss_grad(s, wl.desc, wl.archs, wl.theta, wl.qeq, wl.charge, base["E_cfg"], base["F"], 0.5,
+                        base["q"], 0.4)
+    assert r["loss"] < 1e-20 and np.abs(r["dtheta"]).max() < 1e-10
