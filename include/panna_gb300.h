@@ -436,6 +436,23 @@ panna_status panna_qeq_energy_forces(panna_ctx* ctx, const panna_system* sys, co
                                      double* charges, float* F, panna_stream_t stream);
 
 /*
+ * Training through the charge-equilibration layer (Sec. II.B: reference charges may enter the
+ * loss or be left out).  Loss = the panna_loss_grad loss of the equilibrated energies and
+ * forces (same options and normalisers) + w_charge sum_i (q_i - q_ref_i)^2 when q_ref
+ * [n_atoms] FP64 device is given (NULL: no charge term).  dtheta [P] FP32 = dL/dtheta: the
+ * energy part at fixed charges (their response cancels at the constrained stationary point),
+ * the force part by the double backward with output seeds (1, q_i, q_i^2/2), and the charges'
+ * response dq/dtheta, which the force and charge terms need, from one more solve with the same
+ * matrix.  Outputs as panna_loss_grad, plus the charges [n_atoms] FP64 (may be NULL).  FP32
+ * networks on the CUDA cores.
+ */
+panna_status panna_qeq_loss_grad(panna_ctx* ctx, const panna_system* sys, const float* theta,
+                                 const double* total_charge, const double* E_ref, const float* F_ref,
+                                 double w_force, const double* q_ref, double w_charge, double* loss,
+                                 float* dtheta, double* E_cfg, double* charges, float* F,
+                                 panna_stream_t stream);
+
+/*
  * Precomputed descriptors with stored Jacobians (Sec. II.A: descriptors can be computed
  * once for a whole dataset and reused in every epoch, with their derivatives stored for the
  * forces, at the price of the memory that takes; the default path recomputes them in every

@@ -134,6 +134,7 @@ struct Layout {
     float4* cand_vec = nullptr;
     int2* cand_idx = nullptr;
     double* pos_ref = nullptr;
+    double* qbuf = nullptr;   // charge equilibration: the charges of the forward pass
 };
 
 constexpr int kSplits = 16;
@@ -180,6 +181,7 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, 
     L.F_int = a.take<float>(3 * (size_t)N);
     L.F_tune = a.take<float>(3 * (size_t)N);
     L.E_cfg_int = a.take<double>(C);
+    L.qbuf = a.take<double>(N);
     MlpBuffers& b = L.mb;
     b.G = L.G;
     for (int l = 1; l <= p.L; ++l) {
@@ -1031,6 +1033,92 @@ panna_status panna_qeq_energy_forces(panna_ctx* c, const panna_system* sys, cons
         if (st == PANNA_ERR_BAD_INPUT && c->h_status->code == PANNA_ERR_BAD_INPUT)
             return fail(PANNA_ERR_BAD_INPUT, "configuration or atom %d: invalid input or singular "
                         "charge-equilibration system", c->h_status->bad_index);
+        return st;
+    }
+    return PANNA_OK;
+}
+
+panna_status panna_qeq_loss_grad(panna_ctx* c, const panna_system* sys, const float* theta,
+                                 const double* total_charge, const double* E_ref, const float* F_ref, double w_force,
+                                 const double* q_ref, double w_charge, double* loss, float* dtheta, double* E_cfg,
+                                 double* charges, float* F, panna_stream_t stream)
+{
+    ST(check_system(c, sys));
+    if (!theta || !E_ref || !F_ref || !loss || !dtheta)
+        return fail(PANNA_ERR_INVALID_ARG, "theta, E_ref, F_ref, loss and dtheta are required");
+    if (c->plan.n_out != 3 || !c->qeq_set)
+        return fail(PANNA_ERR_INVALID_ARG, "needs 3-output networks and panna_set_qeq");
+    if (!(w_charge >= 0.0) || !(w_force >= 0.0)) return fail(PANNA_ERR_INVALID_ARG, "weights must be >= 0");
+    if (sys->ghost) return fail(PANNA_ERR_UNSUPPORTED, "charge equilibration of a batch with ghost atoms");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(c->device));
+    const int64_t N = sys->n_atoms;
+    const bool acc = c->ang_mode != 2;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        Layout L;
+        ST(prepare(c, sys, true, false, L, s));
+        int& nl = c->last_launches;
+        nl = 0;
+        for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
+        c->n_marked = 0;
+        float* Fo = F ? F : L.F_int;
+        double* Eo = E_cfg ? E_cfg : L.E_cfg_int;
+        CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
+        stage_mark(c, 0, s);
+        CU(build_neighbors(L.w, c->d, s, &nl));
+        CU(species_order(L.w, c->d.S, s, &nl));
+        CU(mlp_tiles(c->plan, L.w.seg_off, L.mb.tile_start, s, &nl));
+        stage_mark(c, 1, s);
+        int dummy = 0;
+        const int vd = tuned_variant(c, sys, PANNA_MLP_FP32, KV_DESC, s, [&](int vv) {
+            launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &dummy, vv);
+        });
+        CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl, vd));
+        stage_mark(c, 2, s);
+        CU(mlp_forward(c->plan, L.mb, theta, N, s, &nl));
+        stage_mark(c, 4, s);
+        const int ldL = c->plan.ld[c->plan.L];
+        CU(cudaMemsetAsync(Fo, 0, sizeof(float) * 3 * N, s));
+        CU(launch_qeq(c->qeq, L.w, L.mb.A[c->plan.L], ldL, total_charge, L.E_rows, L.qbuf, Fo, L.mb.Ab, ldL, s,
+                      &nl));
+        stage_mark(c, 3, s);
+        CU(mlp_input_grad(c->plan, L.mb, theta, N, L.g, s, &nl, nullptr, true));
+        const int va = tuned_variant(c, sys, PANNA_MLP_FP32, KV_ADJ, s, [&](int vv) {
+            launch_adjoint(L.w, c->d, L.g, L.F_tune, nullptr, acc, vv, s, &dummy);
+        });
+        CU(launch_adjoint(L.w, c->d, L.g, Fo, nullptr, acc, va, s, &nl));
+        CU(launch_cfg_reduce(L.w, L.E_rows, nullptr, Eo, nullptr, nullptr, L.cfg_part, s, &nl));
+        stage_mark(c, 7, s);
+        CU(launch_loss(L.w, c->norm_C, c->norm_N, c->loss_opts, weight_ranges(c->plan), theta, Eo, E_ref, Fo, F_ref,
+                       w_force, loss, L.alpha_cfg, L.u, L.loss_part, s, &nl));
+        stage_mark(c, 5, s);
+        const bool acc_jvp = c->ang_mode == 1;
+        const int vj = tuned_variant(c, sys, PANNA_MLP_FP32, KV_JVP, s, [&](int vv) {
+            launch_jvp(L.w, c->d, L.u, L.wdot, acc_jvp, s, &dummy, vv);
+        });
+        CU(launch_jvp(L.w, c->d, L.u, L.wdot, acc_jvp, s, &nl, vj));
+        stage_mark(c, 6, s);
+        CU(mlp_param_grad(c->plan, L.mb, theta, N, L.wdot, nullptr, dtheta, s, &nl, false, nullptr,
+                          MLP_GRAD_TANGENT));
+        QeqTrain tr{L.qbuf, L.u, L.mb.Ad[c->plan.L], L.alpha_cfg, q_ref, w_charge, L.mb.Adb, loss};
+        CU(launch_qeq_response(c->qeq, L.w, L.mb.A[c->plan.L], ldL, tr, L.mb.Ab, ldL, s, &nl));
+        CU(mlp_param_grad(c->plan, L.mb, theta, N, L.wdot, nullptr, dtheta, s, &nl, false, nullptr,
+                          MLP_GRAD_REVERSE_SEEDED));
+        CU(launch_penalty_grad(c->loss_opts, weight_ranges(c->plan), theta, dtheta, s, &nl));
+        if (charges) CU(cudaMemcpyAsync(charges, L.qbuf, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
+        CU(cudaGetLastError());
+        if (c->async) return PANNA_OK;
+        int need = 0;
+        panna_status st = collect(c, L, s, &need);
+        finish_profile(c);
+        if (st == PANNA_ERR_NEIGHBOR_OVERFLOW && attempt == 0) {
+            c->cap = need + need / 4 + 8;
+            continue;
+        }
+        if (st == PANNA_ERR_UNSUPPORTED)
+            return fail(PANNA_ERR_UNSUPPORTED, "configuration %d: charge equilibration takes non-periodic "
+                        "configurations of at most %d atoms", c->h_status->bad_index, kQeqMax);
         return st;
     }
     return PANNA_OK;

@@ -183,6 +183,21 @@ size_t qeq_smem_bytes(int max_n);
 cudaError_t launch_qeq(const QeqDev& qp, const Work& w, const float* out, int ldo, const double* Qtot,
                        float* E_rows, double* charges, float* F, float* seeds, int lds, cudaStream_t s,
                        int* launches);
+// The charges' response for the loss gradient (see qeq.cu): inputs of the forward pass and of
+// the loss; writes the reverse-pass seeds of the networks' outputs (seeds) and of their
+// tangents (tr.seeds_t), and adds the charge term to *tr.loss
+struct QeqTrain {
+    const double* q;       // [N] charges of the forward pass
+    const float* u;        // [N*3] dL/dF
+    const float* odot;     // output tangents (rows, stride ldo)
+    const double* alpha;   // [C] dL/dE_c
+    const double* q_ref;   // [N] reference charges, or null (no charge term)
+    double w_charge;
+    float* seeds_t;        // rows, stride lds
+    double* loss;
+};
+cudaError_t launch_qeq_response(const QeqDev& qp, const Work& w, const float* out, int ldo, const QeqTrain& tr,
+                                float* seeds, int lds, cudaStream_t s, int* launches);
 
 // Langevin dynamics (md.cu): per species a = (eV/A)/m in A/fs^2 and the thermal velocity
 // scale sigma = sqrt(kB T a) in A/fs

@@ -406,10 +406,10 @@ cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
 
 cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N,
                            const float* wdot, const float* alpha_rows, float* dtheta, cudaStream_t s,
-                           int* launches, bool tan_tc, const WgradTc* wtc)
+                           int* launches, bool tan_tc, const WgradTc* wtc, MlpGradPart part)
 {
     // forward tangent along wdot: zdot_l = adot_{l-1} W_l^T, adot_l = act'(z_l) zdot_l
-    for (int l = tan_tc ? 1 : 0; l < p.L; ++l) {
+    for (int l = tan_tc ? 1 : 0; l < p.L && part != MLP_GRAD_REVERSE_SEEDED; ++l) {
         LayerArgs la = layer_args(p, l, false);
         const float* Ain = l == 0 ? wdot : b.Ad[l];
         k_gemm<true, PRO_NONE, EPI_TAN><<<gemm_grid(p, N, p.ld[l + 1]), 256, 0, s>>>(
@@ -417,9 +417,12 @@ cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
             b.Z[l + 1], p.ld[l + 1]);
         ++*launches;
     }
-    // reverse pass: seeds abar_L = alpha, adotbar_L = -1
-    k_seed<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, p.ld[p.L], alpha_rows, -1.f, b.Ab, b.Adb);
-    ++*launches;
+    if (part == MLP_GRAD_TANGENT) return cudaGetLastError();
+    // reverse pass: seeds abar_L = alpha, adotbar_L = -1 (unless given)
+    if (part != MLP_GRAD_REVERSE_SEEDED) {
+        k_seed<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, p.ld[p.L], alpha_rows, -1.f, b.Ab, b.Adb);
+        ++*launches;
+    }
     for (int l = p.L - 1; l >= 0; --l) {
         const int ldl = p.ld[l + 1];
         k_layer_adjoint<<<(unsigned)((N * ldl + 255) / 256), 256, 0, s>>>(

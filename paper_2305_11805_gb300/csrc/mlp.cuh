@@ -58,11 +58,15 @@ cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const fl
                                  bool split, float* E_rows, float* g, DevStatus* status, cudaStream_t s,
                                  int* launches);
 struct WgradTc;
+// Parts of the weight-gradient pass: both (default); the forward tangent along wdot only (the
+// output tangents land in b.Ad[L]); or the reverse pass only, with the output seeds already in
+// b.Ab (energy part) and b.Adb (force part), rows of stride ld[L]
+enum MlpGradPart { MLP_GRAD_ALL = 0, MLP_GRAD_TANGENT = 1, MLP_GRAD_REVERSE_SEEDED = 2 };
 // tan_tc: the first layer's tangent ran on the tensor cores (tf32_tangent1); wtc (non-null
 // ws): every layer's weight gradient on the tensor cores (tf32_wgrad)
 cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, const float* wdot,
                            const float* alpha_rows, float* dtheta, cudaStream_t s, int* launches,
-                           bool tan_tc = false, const WgradTc* wtc = nullptr);
+                           bool tan_tc = false, const WgradTc* wtc = nullptr, MlpGradPart part = MLP_GRAD_ALL);
 
 // FP32 networks with the first layer on the tensor cores as TF32 hi + lo pairs (mlp_tc.cu).
 // Order per call: tf32_prepare, tf32_forward1, mlp_forward(l0 = 1); mlp_input_grad(ab1) and

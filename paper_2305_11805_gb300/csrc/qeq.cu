@@ -49,10 +49,83 @@ __device__ __forceinline__ float qeq_dist(const double* px, const double* py, co
     return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
 }
 
+// One configuration's system [A 1; 1^T 0] x = rhs in shared memory (FP64): Gaussian
+// elimination with partial pivoting, then back substitution by one warp.  Returns false (the
+// same on every thread) for a zero or non-finite pivot.
+__device__ bool qeq_eliminate(double* M, double* rhs, double* x, int n1, int tid, int nt, int& piv, int& bad)
+{
+    for (int k = 0; k < n1; ++k) {
+        if (tid < 32) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < n1; i += 32) {
+                const double a = fabs(M[i * n1 + k]);
+                if (a > best) { best = a; bi = i; }
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tid == 0) {
+                piv = bi;
+                if (!(best > 0.0) || !isfinite(best)) bad = 1;
+            }
+        }
+        __syncthreads();
+        if (bad) return false;
+        const int p = piv;
+        if (p != k) {
+            for (int j = k + tid; j < n1; j += nt) {
+                const double t = M[k * n1 + j];
+                M[k * n1 + j] = M[p * n1 + j];
+                M[p * n1 + j] = t;
+            }
+            if (tid == 0) {
+                const double t = rhs[k];
+                rhs[k] = rhs[p];
+                rhs[p] = t;
+            }
+        }
+        __syncthreads();
+        const double inv = 1.0 / M[k * n1 + k];
+        const int m = n1 - k - 1;
+        for (int idx = tid; idx < m * m; idx += nt) {
+            const int i = k + 1 + idx / m, j = k + 1 + (idx - (idx / m) * m);
+            M[i * n1 + j] -= M[i * n1 + k] * inv * M[k * n1 + j];
+        }
+        for (int i = k + 1 + tid; i < n1; i += nt) rhs[i] -= M[i * n1 + k] * inv * rhs[k];
+        __syncthreads();
+    }
+    if (tid < 32) {
+        for (int k = n1 - 1; k >= 0; --k) {
+            double acc = 0.0;
+            for (int j = k + 1 + tid; j < n1; j += 32) acc += M[k * n1 + j] * x[j];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (tid == 0) x[k] = (rhs[k] - acc) / M[k * n1 + k];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// TRAIN = false: the charges, energies, pair forces and input-gradient seeds of the forward
+// pass.  TRAIN = true: the charges' response for the loss gradient.  With u = dL/dF, the
+// output tangents odot of the networks along the descriptor tangent of u, and the charge
+// term's slope,
+//   h_i = -(odot_i,1 + q_i odot_i,2 + sum_j q_j K'_ij (x_i - x_j).(u_i - u_j) / r_ij)
+//         + 2 w_q (q_i - q_ref_i),
+// the same matrix gives [A 1; 1^T 0][mu; nu] = [h; 0]; the reverse pass of the networks then
+// takes the seeds (alpha_c, alpha_c q_i - mu_i, alpha_c q_i^2/2 - mu_i q_i) on the outputs and
+// (-1, -q_i, -q_i^2/2) on their tangents.
+template <bool TRAIN>
 __global__ void __launch_bounds__(kQeqThreads)
 k_qeq(QeqDev qp, panna_system sys, int64_t C, const int32_t* __restrict__ row_of_atom, const float* __restrict__ out,
       int ldo, const double* __restrict__ Qtot, float* __restrict__ E_rows, double* __restrict__ charges,
-      float* __restrict__ F, float* __restrict__ seeds, int lds, DevStatus* status, int n_lo, int n_hi)
+      float* __restrict__ F, float* __restrict__ seeds, int lds, DevStatus* status, int n_lo, int n_hi, QeqTrain tr)
 {
     extern __shared__ double sm[];
     __shared__ int piv, bad;
@@ -79,9 +152,10 @@ k_qeq(QeqDev qp, panna_system sys, int64_t C, const int32_t* __restrict__ row_of
             const int s = sys.species[a];
             px[i] = sys.pos[3 * a]; py[i] = sys.pos[3 * a + 1]; pz[i] = sys.pos[3 * a + 2];
             sg[i] = qp.sigma[s];
-            ee[i] = out[r * ldo];
             chi[i] = qp.chi0[s] + out[r * ldo + 1];
             hd[i] = qp.hard0[s] + out[r * ldo + 2];
+            // forward: the local energy; response: the charge of the forward pass
+            ee[i] = TRAIN ? tr.q[a] : out[r * ldo];
         }
         if (tid == 0) bad = 0;
         __syncthreads();
@@ -105,71 +179,61 @@ k_qeq(QeqDev qp, panna_system sys, int64_t C, const int32_t* __restrict__ row_of
             M[idx] = v;
             M[j * n1 + i] = v;
         }
-        for (int i = tid; i < n1; i += nt) rhs[i] = i < n ? -chi[i] : (Qtot ? Qtot[c] : 0.0);
-        __syncthreads();
-
-        // elimination with partial pivoting
-        for (int k = 0; k < n1; ++k) {
-            if (tid < 32) {
-                double best = -1.0;
-                int bi = k;
-                for (int i = k + tid; i < n1; i += 32) {
-                    const double a = fabs(M[i * n1 + k]);
-                    if (a > best) { best = a; bi = i; }
+        if (!TRAIN) {
+            for (int i = tid; i < n1; i += nt) rhs[i] = i < n ? -chi[i] : (Qtot ? Qtot[c] : 0.0);
+        } else {
+            for (int i = tid; i < n1; i += nt) {
+                if (i == n) {
+                    rhs[i] = 0.0;
+                    continue;
                 }
-    #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) {
-                    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                const int64_t a = a0 + i;
+                const int64_t r = row_of_atom[a];
+                const double qi = ee[i];
+                const float ux = tr.u[3 * a], uy = tr.u[3 * a + 1], uz = tr.u[3 * a + 2];
+                double v = tr.odot[r * ldo + 1] + qi * tr.odot[r * ldo + 2];
+                for (int j = 0; j < n; ++j) {
+                    if (j == i) continue;
+                    float dx, dy, dz, K, dK;
+                    const float rr = qeq_dist(px, py, pz, i, j, dx, dy, dz);
+                    qeq_pair(rr, (float)sg[i], (float)sg[j], (float)qp.ke, K, dK);
+                    const int64_t b = a0 + j;
+                    const float du = dx * (ux - tr.u[3 * b]) + dy * (uy - tr.u[3 * b + 1]) + dz * (uz - tr.u[3 * b + 2]);
+                    v += ee[j] * (double)(dK * du / rr);
                 }
-                if (tid == 0) {
-                    piv = bi;
-                    if (!(best > 0.0) || !isfinite(best)) bad = 1;
-                }
+                double h = -v;
+                if (tr.q_ref) h += 2.0 * tr.w_charge * (qi - tr.q_ref[a]);
+                rhs[i] = h;
             }
-            __syncthreads();
-            if (bad) break;
-            const int p = piv;
-            if (p != k) {
-                for (int j = k + tid; j < n1; j += nt) {
-                    const double t = M[k * n1 + j];
-                    M[k * n1 + j] = M[p * n1 + j];
-                    M[p * n1 + j] = t;
-                }
-                if (tid == 0) {
-                    const double t = rhs[k];
-                    rhs[k] = rhs[p];
-                    rhs[p] = t;
-                }
-            }
-            __syncthreads();
-            const double inv = 1.0 / M[k * n1 + k];
-            const int m = n1 - k - 1;
-            for (int idx = tid; idx < m * m; idx += nt) {
-                const int i = k + 1 + idx / m, j = k + 1 + (idx - (idx / m) * m);
-                M[i * n1 + j] -= M[i * n1 + k] * inv * M[k * n1 + j];
-            }
-            for (int i = k + 1 + tid; i < n1; i += nt) rhs[i] -= M[i * n1 + k] * inv * rhs[k];
-            __syncthreads();
         }
-        if (bad) {
+        __syncthreads();
+        if (!qeq_eliminate(M, rhs, x, n1, tid, nt, piv, bad)) {
             if (tid == 0) set_status(status, PANNA_ERR_BAD_INPUT, (int)c);
             continue;
         }
-        // back substitution (one warp)
-        if (tid < 32) {
-            for (int k = n1 - 1; k >= 0; --k) {
-                double acc = 0.0;
-                for (int j = k + 1 + tid; j < n1; j += 32) acc += M[k * n1 + j] * x[j];
-    #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (tid == 0) x[k] = (rhs[k] - acc) / M[k * n1 + k];
-                __syncwarp();
-            }
-        }
-        __syncthreads();
 
+        if (TRAIN) {
+            const double al = tr.alpha[c];
+            double lq = 0.0;
+            for (int i = tid; i < n; i += nt) {
+                const int64_t a = a0 + i;
+                const int64_t r = row_of_atom[a];
+                const double qi = ee[i], mu = x[i];
+                seeds[r * lds] = (float)al;
+                seeds[r * lds + 1] = (float)(al * qi - mu);
+                seeds[r * lds + 2] = (float)(al * 0.5 * qi * qi - mu * qi);
+                tr.seeds_t[r * lds] = -1.f;
+                tr.seeds_t[r * lds + 1] = (float)(-qi);
+                tr.seeds_t[r * lds + 2] = (float)(-0.5 * qi * qi);
+                if (tr.q_ref) lq += tr.w_charge * (qi - tr.q_ref[a]) * (qi - tr.q_ref[a]);
+            }
+            if (tr.q_ref) {
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) lq += __shfl_xor_sync(0xffffffffu, lq, o);
+                if ((tid & 31) == 0 && lq != 0.0) atomicAdd(tr.loss, lq);
+            }
+            continue;
+        }
         // energies, pair forces, network seeds
         for (int i = tid; i < n; i += nt) {
             const double qi = x[i];
@@ -204,13 +268,14 @@ size_t qeq_smem_bytes(int max_n)
     return (n1 * n1 + 2 * n1 + 7 * n) * sizeof(double);
 }
 
-cudaError_t launch_qeq(const QeqDev& qp, const Work& w, const float* out, int ldo, const double* Qtot,
-                       float* E_rows, double* charges, float* F, float* seeds, int lds, cudaStream_t s,
-                       int* launches)
+template <bool TRAIN>
+static cudaError_t qeq_launch(const QeqDev& qp, const Work& w, const float* out, int ldo, const double* Qtot,
+                              float* E_rows, double* charges, float* F, float* seeds, int lds, const QeqTrain& tr,
+                              cudaStream_t s, int* launches)
 {
     if (w.C == 0) return cudaSuccess;
     const int classes[3] = {0, 32, kQeqMax};
-    cudaError_t e = cudaFuncSetAttribute(k_qeq, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_qeq<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)qeq_smem_bytes(kQeqMax));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -221,14 +286,28 @@ cudaError_t launch_qeq(const QeqDev& qp, const Work& w, const float* out, int ld
         // also reports configurations beyond kQeqMax
         const size_t smem = qeq_smem_bytes(classes[k + 1]);
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qeq, kQeqThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qeq<TRAIN>, kQeqThreads, smem);
         int64_t nb = (int64_t)(sms > 0 ? sms : 1) * (per > 0 ? per : 1);
         if (nb > w.C) nb = w.C;
-        k_qeq<<<(unsigned)nb, kQeqThreads, smem, s>>>(qp, *w.sys, w.C, w.row_of_atom, out, ldo, Qtot, E_rows,
-                                                      charges, F, seeds, lds, w.status, classes[k], classes[k + 1]);
+        k_qeq<TRAIN><<<(unsigned)nb, kQeqThreads, smem, s>>>(qp, *w.sys, w.C, w.row_of_atom, out, ldo, Qtot, E_rows,
+                                                             charges, F, seeds, lds, w.status, classes[k],
+                                                             classes[k + 1], tr);
         ++*launches;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_qeq(const QeqDev& qp, const Work& w, const float* out, int ldo, const double* Qtot,
+                       float* E_rows, double* charges, float* F, float* seeds, int lds, cudaStream_t s,
+                       int* launches)
+{
+    return qeq_launch<false>(qp, w, out, ldo, Qtot, E_rows, charges, F, seeds, lds, QeqTrain{}, s, launches);
+}
+
+cudaError_t launch_qeq_response(const QeqDev& qp, const Work& w, const float* out, int ldo, const QeqTrain& tr,
+                                float* seeds, int lds, cudaStream_t s, int* launches)
+{
+    return qeq_launch<true>(qp, w, out, ldo, nullptr, nullptr, nullptr, nullptr, seeds, lds, tr, s, launches);
 }
 
 }  // namespace panna

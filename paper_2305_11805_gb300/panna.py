@@ -131,6 +131,8 @@ def load(path: str = LIB_PATH):
         "panna_replay": (i32, [_vp, _vp]),
         "panna_set_qeq": (i32, [_vp, C.POINTER(panna_qeq_params)]),
         "panna_qeq_energy_forces": (i32, [_vp, C.POINTER(panna_system), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "panna_qeq_loss_grad": (i32, [_vp, C.POINTER(panna_system), _vp, _vp, _vp, _vp, f64, _vp, f64, _vp, _vp, _vp,
+                                      _vp, _vp, _vp]),
         "panna_store_plan": (i32, [_vp, C.POINTER(panna_system), C.POINTER(panna_store_info), _vp]),
         "panna_store_sections": (i32, [_vp, C.POINTER(panna_store_info), C.POINTER(i64)]),
         "panna_store_build": (i32, [_vp, C.POINTER(panna_system), C.POINTER(panna_store_info), _vp, _vp]),
@@ -156,7 +158,7 @@ def exported_symbols() -> Sequence[str]:
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
             "panna_descriptors_static", "panna_capture", "panna_replay", "panna_store_plan",
             "panna_store_sections", "panna_store_build", "panna_store_energy_forces", "panna_store_loss_grad",
-            "panna_set_qeq", "panna_qeq_energy_forces"]
+            "panna_set_qeq", "panna_qeq_energy_forces", "panna_qeq_loss_grad"]
 
 
 def _check(status: int):
@@ -344,6 +346,13 @@ def panna_qeq_energy_forces(ctx: int, sysd: "DeviceSystem", theta, total_charge,
                             stream=None):
     _check(load().panna_qeq_energy_forces(ctx, C.byref(sysd.s), _ptr(theta), _ptr(total_charge), _ptr(E_cfg),
                                           _ptr(E_atom), _ptr(charges), _ptr(F), _stream(stream)))
+
+
+def panna_qeq_loss_grad(ctx: int, sysd: "DeviceSystem", theta, total_charge, E_ref, F_ref, w_force: float, q_ref,
+                        w_charge: float, loss, dtheta, E_cfg=None, charges=None, F=None, stream=None):
+    _check(load().panna_qeq_loss_grad(ctx, C.byref(sysd.s), _ptr(theta), _ptr(total_charge), _ptr(E_ref), _ptr(F_ref),
+                                      float(w_force), _ptr(q_ref), float(w_charge), _ptr(loss), _ptr(dtheta),
+                                      _ptr(E_cfg), _ptr(charges), _ptr(F), _stream(stream)))
 
 
 def panna_store_plan(ctx: int, sysd: "DeviceSystem", stream=None) -> panna_store_info:

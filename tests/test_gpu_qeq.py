@@ -144,3 +144,35 @@ def test_qeq_arguments(torch_cuda):
     with pytest.raises(P.PannaError) as ei:
         P.panna_set_qeq(pot1.ctx, [1.0] * 4, [1.0] * 4, [1.0] * 4)
     assert ei.value.status == P.PANNA_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("with_charges", [False, True])
+def test_qeq_training_gradient_matches_oracle(torch_cuda, with_charges):
+    torch = torch_cuda
+    wl = W.make("nacl64")
+    s = wl.system
+    th32 = wl.theta.astype(np.float32)
+    th64 = th32.astype(np.float64)
+    base = O.qeq_batch(s, wl.desc, wl.archs, th64, wl.qeq, wl.charge)
+    rng = np.random.default_rng(4)
+    e_ref = base["E_cfg"] + rng.normal(0, 0.3, s.n_cfg) * np.diff(s.atom_off)
+    f_ref = (base["F"] + rng.normal(0, 0.2, base["F"].shape)).astype(np.float32).astype(np.float64)
+    q_ref = base["q"] + rng.normal(0, 0.05, s.n_atoms) if with_charges else None
+    w_force, w_q = 0.7, 0.3
+    ref = O.qeq_loss_grad(s, wl.desc, wl.archs, th64, wl.qeq, wl.charge, e_ref, f_ref, w_force, q_ref, w_q)
+    pot = _pot(wl)
+    dev = lambda a, dt=torch.float64: None if a is None else torch.as_tensor(a, dtype=dt, device="cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(pot.P, dtype=torch.float32, device="cuda")
+    E = torch.empty(s.n_cfg, dtype=torch.float64, device="cuda")
+    q = torch.empty(s.n_atoms, dtype=torch.float64, device="cuda")
+    F = torch.empty((s.n_atoms, 3), dtype=torch.float32, device="cuda")
+    P.panna_qeq_loss_grad(pot.ctx, P.DeviceSystem(s), torch.as_tensor(th32, device="cuda"), dev(wl.charge), dev(e_ref),
+                          dev(f_ref, torch.float32), w_force, dev(q_ref), w_q, loss, g, E, q, F)
+    lerr = abs(loss.item() - ref["loss"]) / abs(ref["loss"])
+    errs = H.layer_errors(wl.archs, g.cpu().numpy().astype(np.float64), ref["dtheta"])
+    ferr = H.force_error(F.cpu().numpy().astype(np.float64), ref["F"])[0]
+    qerr = float(np.abs(q.cpu().numpy() - ref["q"]).max())
+    print("qeq training step (charges %s): loss %.3g, dtheta worst layer %.3g, forces %.3g, charges %.3g" % (
+        with_charges, lerr, max(errs), ferr, qerr))
+    assert lerr <= 1e-5 and max(errs) <= H.TOL_DTHETA and ferr <= H.TOL_F_FP32 and qerr <= 1e-5
