@@ -618,6 +618,28 @@ def run_qeq(args):
     ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps
     stage = {k: round(v / args.steps, 4) for k, v in sm.items() if v > 0}
 
+    # training step through the charge layer (energy + force loss and its gradient), timed the
+    # same way and reported beside the evaluation
+    rng = np.random.default_rng(args.seed)
+    e_ref = torch.as_tensor(rng.normal(0, 1, C), dtype=torch.float64, device="cuda") + E
+    f_ref = F + torch.as_tensor(rng.normal(0, 0.2, (N, 3)), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty(pot.P, dtype=torch.float32, device="cuda")
+
+    def train_step():
+        P.panna_qeq_loss_grad(pot.ctx, sysd, theta, Q, e_ref, f_ref, 0.1, None, 0.0, loss, grad)
+
+    for _ in range(args.warmup):
+        train_step()
+    torch.cuda.synchronize()
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    for k in range(args.steps):
+        train_step()
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    train_ms = t0e.elapsed_time(t1e) / args.steps
+
     # end to end: positions, species, offsets and total charges from pinned host memory,
     # energies and charges read back
     hs = [torch.as_tensor(a).pin_memory() for a in (wl.system.atom_off, wl.system.pos, wl.system.species,
@@ -648,7 +670,8 @@ def run_qeq(args):
            "config": {"workload": "4096 NaCl clusters (Na9Cl8+ / Na8Cl8+ alternating, +1 e each), %d atoms; "
                                   "descriptor D=%d, networks 45-15-15-3, Gaussian charges (sigma Na 1.0, Cl 1.2 A)"
                                   % (N, wl.desc.D), "l2": "flushed between steps (256 MiB write)",
-                      "stage_ms_per_step": stage},
+                      "stage_ms_per_step": stage, "training_step_ms": train_ms,
+                      "training_atoms_per_s": N / (train_ms * 1e-3)},
            "e2e": {"value": e2e, "unit": UNIT,
                    "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in hs),
                    "d2h_bytes_per_step": hE.numel() * 8 + hq.numel() * 8},

@@ -49,66 +49,131 @@ __device__ __forceinline__ float qeq_dist(const double* px, const double* py, co
     return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
 }
 
-// One configuration's system [A 1; 1^T 0] x = rhs in shared memory (FP64): Gaussian
-// elimination with partial pivoting, then back substitution by one warp.  Returns false (the
-// same on every thread) for a zero or non-finite pivot.
-__device__ bool qeq_eliminate(double* M, double* rhs, double* x, int n1, int tid, int nt, int& piv, int& bad)
+// Shared-memory workspace of one configuration (n atoms, n1 = n + 1 unknowns): the FP64
+// matrix (kept for residuals), its FP32 LU factors, the permutation, right-hand side,
+// solution, residual and correction, and the per-atom staging arrays.
+struct QeqShared {
+    double* M; float* LU; int* perm; double* rhs; double* x; double* res; float* d;
+    double* px; double* py; double* pz; double* sg; double* chi; double* hd; double* ee;
+};
+
+__host__ __device__ inline size_t qeq_shared_bytes(int n)
 {
+    const size_t n1 = (size_t)n + 1;
+    const size_t dbl = n1 * n1 + 3 * n1 + 7 * (size_t)n;   // M, rhs, x, res, staging
+    const size_t flt = n1 * n1 + n1;                       // LU, d
+    return dbl * sizeof(double) + ((flt * sizeof(float) + n1 * sizeof(int) + 7) & ~(size_t)7);
+}
+
+__device__ inline QeqShared qeq_carve(double* base, int n)
+{
+    const int n1 = n + 1;
+    QeqShared q;
+    q.M = base;
+    q.rhs = q.M + n1 * n1; q.x = q.rhs + n1; q.res = q.x + n1;
+    q.px = q.res + n1; q.py = q.px + n; q.pz = q.py + n;
+    q.sg = q.pz + n; q.chi = q.sg + n; q.hd = q.chi + n; q.ee = q.hd + n;
+    q.LU = reinterpret_cast<float*>(q.ee + n);
+    q.d = q.LU + n1 * n1;
+    q.perm = reinterpret_cast<int*>(q.d + n1);
+    return q;
+}
+
+// x = LU^-1 P r in FP32 (one warp): forward substitution with the unit lower factor, then
+// back substitution with the upper one; d holds the result
+__device__ void qeq_lu_apply(const QeqShared& q, int n1, const double* r, int tid)
+{
+    if (tid >= 32) return;
+    for (int k = 0; k < n1; ++k) {
+        float acc = 0.f;
+        for (int j = tid; j < k; j += 32) acc += q.LU[k * n1 + j] * q.d[j];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (tid == 0) q.d[k] = (float)r[q.perm[k]] - acc;
+        __syncwarp();
+    }
+    for (int k = n1 - 1; k >= 0; --k) {
+        float acc = 0.f;
+        for (int j = k + 1 + tid; j < n1; j += 32) acc += q.LU[k * n1 + j] * q.d[j];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (tid == 0) q.d[k] = (q.d[k] - acc) / q.LU[k * n1 + k];
+        __syncwarp();
+    }
+}
+
+// Solves [A 1; 1^T 0] x = rhs (q.M, q.rhs) into q.x: LU factors with partial pivoting in FP32,
+// then iterative refinement with FP64 residuals r = rhs - M x (two steps take the FP32
+// solution to about FP64 accuracy for these well-conditioned systems; the FP64 work is
+// O(n^2) instead of the O(n^3) of an FP64 factorisation, which the GB300's narrow FP64 pipe
+// made the slowest part of the call).  Returns false (the same on every thread) for a zero
+// or non-finite pivot.
+__device__ bool qeq_solve(const QeqShared& q, int n1, int tid, int nt, int& piv, int& bad)
+{
+    for (int idx = tid; idx < n1 * n1; idx += nt) q.LU[idx] = (float)q.M[idx];
+    for (int i = tid; i < n1; i += nt) q.perm[i] = i;
+    __syncthreads();
     for (int k = 0; k < n1; ++k) {
         if (tid < 32) {
-            double best = -1.0;
+            float best = -1.f;
             int bi = k;
             for (int i = k + tid; i < n1; i += 32) {
-                const double a = fabs(M[i * n1 + k]);
+                const float a = fabsf(q.LU[i * n1 + k]);
                 if (a > best) { best = a; bi = i; }
             }
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
             if (tid == 0) {
                 piv = bi;
-                if (!(best > 0.0) || !isfinite(best)) bad = 1;
+                if (!(best > 0.f) || !isfinite(best)) bad = 1;
             }
         }
         __syncthreads();
         if (bad) return false;
         const int p = piv;
         if (p != k) {
-            for (int j = k + tid; j < n1; j += nt) {
-                const double t = M[k * n1 + j];
-                M[k * n1 + j] = M[p * n1 + j];
-                M[p * n1 + j] = t;
+            for (int j = tid; j < n1; j += nt) {
+                const float t = q.LU[k * n1 + j];
+                q.LU[k * n1 + j] = q.LU[p * n1 + j];
+                q.LU[p * n1 + j] = t;
             }
             if (tid == 0) {
-                const double t = rhs[k];
-                rhs[k] = rhs[p];
-                rhs[p] = t;
+                const int t = q.perm[k];
+                q.perm[k] = q.perm[p];
+                q.perm[p] = t;
             }
         }
         __syncthreads();
-        const double inv = 1.0 / M[k * n1 + k];
+        const float inv = 1.f / q.LU[k * n1 + k];
+        for (int i = k + 1 + tid; i < n1; i += nt) q.LU[i * n1 + k] *= inv;   // multipliers
+        __syncthreads();
         const int m = n1 - k - 1;
         for (int idx = tid; idx < m * m; idx += nt) {
             const int i = k + 1 + idx / m, j = k + 1 + (idx - (idx / m) * m);
-            M[i * n1 + j] -= M[i * n1 + k] * inv * M[k * n1 + j];
+            q.LU[i * n1 + j] -= q.LU[i * n1 + k] * q.LU[k * n1 + j];
         }
-        for (int i = k + 1 + tid; i < n1; i += nt) rhs[i] -= M[i * n1 + k] * inv * rhs[k];
         __syncthreads();
     }
-    if (tid < 32) {
-        for (int k = n1 - 1; k >= 0; --k) {
-            double acc = 0.0;
-            for (int j = k + 1 + tid; j < n1; j += 32) acc += M[k * n1 + j] * x[j];
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (tid == 0) x[k] = (rhs[k] - acc) / M[k * n1 + k];
-            __syncwarp();
-        }
-    }
+    // solution and two refinement steps
+    for (int i = tid; i < n1; i += nt) { q.x[i] = 0.0; q.res[i] = q.rhs[i]; }
     __syncthreads();
+    for (int it = 0; it < 3; ++it) {
+        qeq_lu_apply(q, n1, q.res, tid);
+        __syncthreads();
+        for (int i = tid; i < n1; i += nt) q.x[i] += (double)q.d[i];
+        __syncthreads();
+        if (it == 2) break;
+        for (int i = tid; i < n1; i += nt) {
+            double r = q.rhs[i];
+            for (int j = 0; j < n1; ++j) r -= q.M[i * n1 + j] * q.x[j];
+            q.res[i] = r;
+        }
+        __syncthreads();
+    }
     return true;
 }
 
@@ -141,11 +206,10 @@ k_qeq(QeqDev qp, panna_system sys, int64_t C, const int32_t* __restrict__ row_of
         }
         __syncthreads();   // the previous configuration's shared data is no longer read
         const int n1 = n + 1;
-        double* M = sm;
-        double* rhs = M + n1 * n1;
-        double* x = rhs + n1;
-        double* px = x + n1; double* py = px + n; double* pz = py + n;
-        double* sg = pz + n; double* chi = sg + n; double* hd = chi + n; double* ee = hd + n;
+        const QeqShared qs = qeq_carve(sm, n);
+        double* M = qs.M; double* rhs = qs.rhs; double* x = qs.x;
+        double* px = qs.px; double* py = qs.py; double* pz = qs.pz;
+        double* sg = qs.sg; double* chi = qs.chi; double* hd = qs.hd; double* ee = qs.ee;
         for (int i = tid; i < n; i += nt) {
             const int64_t a = a0 + i;
             const int64_t r = row_of_atom[a];
@@ -207,7 +271,7 @@ k_qeq(QeqDev qp, panna_system sys, int64_t C, const int32_t* __restrict__ row_of
             }
         }
         __syncthreads();
-        if (!qeq_eliminate(M, rhs, x, n1, tid, nt, piv, bad)) {
+        if (!qeq_solve(qs, n1, tid, nt, piv, bad)) {
             if (tid == 0) set_status(status, PANNA_ERR_BAD_INPUT, (int)c);
             continue;
         }
@@ -236,25 +300,28 @@ k_qeq(QeqDev qp, panna_system sys, int64_t C, const int32_t* __restrict__ row_of
         }
         // energies, pair forces, network seeds
         for (int i = tid; i < n; i += nt) {
+            // sums of O(n) single-precision terms (FP32 accuracy is what the outputs carry)
             const double qi = x[i];
-            double kq = self / sg[i] * qi, fx = 0.0, fy = 0.0, fz = 0.0;
+            const float qf = (float)qi;
+            float kq = (float)(self / sg[i]) * qf, fx = 0.f, fy = 0.f, fz = 0.f;
             const float si = (float)sg[i], ke = (float)qp.ke;
             for (int j = 0; j < n; ++j) {
                 if (j == i) continue;
                 float dx, dy, dz, K, dK;
                 const float r = qeq_dist(px, py, pz, i, j, dx, dy, dz);
                 qeq_pair(r, si, (float)sg[j], ke, K, dK);
-                kq += (double)K * x[j];
-                const double f = -qi * x[j] * (double)(dK / r);
-                fx += f * dx; fy += f * dy; fz += f * dz;
+                const float xj = (float)x[j];
+                kq = fmaf(K, xj, kq);
+                const float f = -qf * xj * (dK / r);
+                fx = fmaf(f, dx, fx); fy = fmaf(f, dy, fy); fz = fmaf(f, dz, fz);
             }
             const int64_t a = a0 + i;
             const int64_t r = row_of_atom[a];
-            E_rows[r] = (float)(ee[i] + chi[i] * qi + 0.5 * hd[i] * qi * qi + 0.5 * qi * kq);
+            E_rows[r] = (float)(ee[i] + chi[i] * qi + 0.5 * hd[i] * qi * qi + 0.5 * qi * (double)kq);
             if (charges) charges[a] = qi;
-            F[3 * a] += (float)fx;
-            F[3 * a + 1] += (float)fy;
-            F[3 * a + 2] += (float)fz;
+            F[3 * a] += fx;
+            F[3 * a + 1] += fy;
+            F[3 * a + 2] += fz;
             seeds[r * lds] = 1.f;
             seeds[r * lds + 1] = (float)qi;
             seeds[r * lds + 2] = (float)(0.5 * qi * qi);
@@ -262,11 +329,7 @@ k_qeq(QeqDev qp, panna_system sys, int64_t C, const int32_t* __restrict__ row_of
     }
 }
 
-size_t qeq_smem_bytes(int max_n)
-{
-    const size_t n = (size_t)max_n, n1 = n + 1;
-    return (n1 * n1 + 2 * n1 + 7 * n) * sizeof(double);
-}
+size_t qeq_smem_bytes(int max_n) { return qeq_shared_bytes(max_n); }
 
 template <bool TRAIN>
 static cudaError_t qeq_launch(const QeqDev& qp, const Work& w, const float* out, int ldo, const double* Qtot,
