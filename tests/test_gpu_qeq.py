@@ -176,3 +176,28 @@ def test_qeq_training_gradient_matches_oracle(torch_cuda, with_charges):
     print("qeq training step (charges %s): loss %.3g, dtheta worst layer %.3g, forces %.3g, charges %.3g" % (
         with_charges, lerr, max(errs), ferr, qerr))
     assert lerr <= 1e-5 and max(errs) <= H.TOL_DTHETA and ferr <= H.TOL_F_FP32 and qerr <= 1e-5
+
+
+def test_qeq_nacl4096_sampled_clusters(torch_cuda):
+    """The benchmark's batch (4096 clusters) in one call; the clusters are independent, so the
+    oracle redoes a sample of them one by one."""
+    torch = torch_cuda
+    wl = W.make("nacl4096")
+    s = wl.system
+    pot = _pot(wl)
+    th32 = wl.theta.astype(np.float32)
+    E, Ea, q, F = pot.qeq_energy_forces(P.DeviceSystem(s), torch.as_tensor(th32, device="cuda"),
+                                        torch.as_tensor(wl.charge, device="cuda"))
+    E, q, F = E.cpu().numpy(), q.cpu().numpy(), F.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(9)
+    cfgs = sorted(rng.choice(s.n_cfg, 24, replace=False).tolist())
+    sub = s.subset(cfgs)
+    ref = O.qeq_batch(sub, wl.desc, wl.archs, th32.astype(np.float64), wl.qeq, wl.charge[cfgs])
+    rows = np.concatenate([np.arange(s.atom_off[c], s.atom_off[c + 1]) for c in cfgs])
+    eerr = float(np.abs(E[cfgs] - ref["E_cfg"]).max() / np.abs(ref["E_atom"]).sum())
+    qerr = float(np.abs(q[rows] - ref["q"]).max())
+    ferr = float(np.abs(F[rows] - ref["F"]).max() / np.sqrt((F ** 2).mean()))
+    sums = np.add.reduceat(q, s.atom_off[:-1])
+    print("nacl4096 (%d atoms), 24 sampled clusters: energies %.3g, charges %.3g, forces %.3g; "
+          "total charges within %.3g of +1" % (s.n_atoms, eerr, qerr, ferr, np.abs(sums - 1).max()))
+    assert eerr <= H.TOL_E and qerr <= 1e-5 and ferr <= H.TOL_F_FP32 and np.abs(sums - 1).max() <= 1e-9
