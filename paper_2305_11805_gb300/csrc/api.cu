@@ -173,6 +173,12 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, 
     w.atom_of_row = a.take<int32_t>(N);
     w.seg_off = a.take<int32_t>(S + 1);
     w.blk_counts = a.take<int32_t>(((N + 1023) / 1024 + 1) * S);
+    w.split_part = nullptr;
+    w.split_rows = 0;
+    if (N > 0 && N < kSplitAtoms) {
+        w.split_rows = N * kMaxSplits;
+        w.split_part = a.take<float>((size_t)w.split_rows * D);
+    }
     L.G = a.take<float>((size_t)N * D);
     L.g = a.take<float>((size_t)N * D);
     L.E_rows = a.take<float>(N);

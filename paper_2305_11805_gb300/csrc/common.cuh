@@ -106,7 +106,17 @@ struct Work {
     int32_t* atom_of_row;        // [N]
     int32_t* seg_off;            // [S+1] rows of species s: seg_off[s]..seg_off[s+1]-1
     int32_t* blk_counts;         // species sort scratch
+    // small batches: per-split partial descriptor rows [split_rows / N][N][D] (null: no splits)
+    float* split_part;
+    int64_t split_rows;
 };
+
+// Small batches spread the angular pairs of one atom over several warps (descriptor and
+// adjoint, blocked layout): below kSplitAtoms atoms, up to kMaxSplits warps per atom, aiming
+// at kSplitTargetWarps warps in all
+constexpr int64_t kSplitAtoms = 1216;
+constexpr int kMaxSplits = 16;
+constexpr int64_t kSplitTargetWarps = 2432;
 
 // launch helpers implemented in the .cu files
 int64_t scan_scratch_elems(int64_t n);
