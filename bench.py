@@ -317,7 +317,8 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel.  The descriptor, adjoint and JVP stages are one
     # kernel launch each (FP32 CUDA-core arithmetic, "alu"); algorithmic FLOPs per unit are
-    # the minimal operation counts of the design doc.  The network stages are several kernels
+    # minimal operation counts (geometry, 8 zeta-powers by 7 multiplies, 8 Gaussians, the
+    # 64-term outer product per pair of an 8 x 8 tile).  The network stages are several kernels
     # each and are listed per stage only.
     peaks, peak_kind = load_peaks()
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)

@@ -5,7 +5,7 @@ import numpy as np
 
 from paper_2305_11805_gb300 import workloads as W
 
-# Tolerances (see DESIGN.md "Readings"): FP32 path.
+# Tolerances: FP32 path.
 TOL_F_FP32 = 1e-5        # max |dF| / RMS(F_oracle)
 TOL_F_BF16 = 1e-2
 TOL_E = 1e-5             # |dE_c| / sum_i |E_i|
