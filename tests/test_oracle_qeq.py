@@ -179,3 +179,20 @@ def test_qeq_loss_without_labels_terms():
     r = O.qeq_loss_grad(s, wl.desc, wl.archs, wl.theta, wl.qeq, wl.charge, base["E_cfg"], base["F"], 0.5,
                         base["q"], 0.4)
     assert r["loss"] < 1e-20 and np.abs(r["dtheta"]).max() < 1e-10
+
+
+def test_nacl_workload_shapes():
+    """The clusters are those of the paper's NaCl experiment: Na9Cl8+ and Na8Cl8+ alternating,
+    each with a total charge of +1, rock-salt distances (nearest neighbours near a/2)."""
+    wl = W.make("nacl64")
+    s = wl.system
+    assert s.n_cfg == 64 and wl.desc.D == 45 and wl.archs[0].widths == (45, 15, 15, 3)
+    for c in range(s.n_cfg):
+        sp = s.species[s.atom_off[c]:s.atom_off[c + 1]]
+        na, cl = int((sp == 0).sum()), int((sp == 1).sum())
+        assert (na, cl) == ((9, 8) if c % 2 == 0 else (8, 8))
+        x = s.pos[s.atom_off[c]:s.atom_off[c + 1]]
+        d = np.linalg.norm(x[:, None] - x[None], axis=-1)[np.triu_indices(len(x), 1)]
+        assert 2.2 < d.min() and abs(np.sort(d)[0:10].mean() - 2.82) < 0.3
+    np.testing.assert_array_equal(wl.charge, np.ones(s.n_cfg))
+    assert not s.pbc.any()
