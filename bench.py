@@ -378,7 +378,7 @@ def run_ragged(args):
     build.build()
     from paper_2305_11805_gb300 import panna as P
     from paper_2305_11805_gb300 import workloads as W
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(dist_env()[2])
     wl = W.make("ragged4096", seed=args.seed)
     s = wl.system
     N, C = s.n_atoms, s.n_cfg
@@ -456,7 +456,7 @@ def run_stored(args):
     build.build()
     from paper_2305_11805_gb300 import panna as P
     from paper_2305_11805_gb300 import workloads as W
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(dist_env()[2])
     wl = W.make(WORKLOAD, seed=args.seed)
     N, C = wl.system.n_atoms, wl.system.n_cfg
     pot = P.Potential(wl.desc, wl.archs)
@@ -575,7 +575,7 @@ def run_qeq(args):
     build.build()
     from paper_2305_11805_gb300 import panna as P
     from paper_2305_11805_gb300 import workloads as W
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(dist_env()[2])
     wl = W.make("nacl4096", seed=args.seed)
     N, C = wl.system.n_atoms, wl.system.n_cfg
     pot = P.Potential(wl.desc, wl.archs)
@@ -691,7 +691,7 @@ def run_md(args):
     build.build()
     from paper_2305_11805_gb300 import panna as P
     from paper_2305_11805_gb300 import workloads as W
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(dist_env()[2])
     mass, T, dt, gam, skin = [12.011], 300.0, 0.5, 0.01, 0.5
     out = {"metric": "Langevin MD time per step per atom", "unit": "ms", "higher_is_better": False,
            "n_gpus": 1, "dtype": "fp32", "data": "synthetic",
@@ -742,6 +742,14 @@ def main():
     ap.add_argument("--ref-molecules", type=int, default=24)
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "ragged4096", "md", "stored", "qeq"])
     args = ap.parse_args()
+    if args.workload != WORKLOAD and args.impl == "ours":
+        # the secondary workloads are single-GPU measurements: under torchrun rank 0 runs on
+        # its own device and prints the line, the other ranks exit without work
+        rank, world, local = dist_env()
+        if rank != 0:
+            return 0
+        import torch
+        torch.cuda.set_device(local)
     if args.workload == "ragged4096" and args.impl == "ours":
         return run_ragged(args)
     if args.workload == "md" and args.impl == "ours":
