@@ -1,19 +1,28 @@
-"""Benchmark: one training step of the PANNA energy + force potential (arXiv 2305.11805).
+"""Benchmark of the PANNA energy + force potential (arXiv 2305.11805) on one GB300 per rank.
 
-Workload (default): 1024 isolated molecules of 5..29 atoms (H/C/N/O 0.5/0.3/0.1/0.1,
-random bonded chains, no PBC, rc 5.2 A), 4-species descriptor of size 768 (32 radial
-shells per species, 8 x 8 angular bins per species pair), per-species networks
-768-128-32-1 with Gaussian activations.  One step = neighbour search, descriptors,
-networks, energies, forces (adjoint), energy + 0.1 force MSE loss and its gradient with
-respect to every network parameter (descriptor JVP + double backward), all in the CUDA
-library, FP32 kernels and FP64 reductions.  Metric: atoms per second.
+Default workload ragged4096: energies and forces of a ragged batch of 4096 periodic cubic
+boxes of 32..4096 atoms (log-uniform; 3.37 M atoms; 3 species in Dirichlet(1,1,1) proportions;
+0.05 atoms/A^3; rc 5.5 A), descriptor D = 480 (32 radial shells per species, 8 x 8 angular
+bins per species pair), per-species networks 480-128-32-1 (Gaussian), BF16 networks with FP32
+accumulation, FP32 descriptors and adjoint, FP64 energy sums.  One step = neighbour search,
+descriptors, networks, energies, forces, run as one captured CUDA graph.  Metric: atoms/s,
+stated with the measured force error against the FP64 oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload ragged4096|fcc1m|water32k|diamond64|molecules1024|stored|qeq|md]
 
---impl reference times the FP64 CPU oracle (single thread) on a bounded sample of the
-same workload.  Under torchrun each rank runs its own batch of 1024 molecules (weak
-scaling), normalises its loss by the global counts, and the gradients are summed over
-ranks with one all-reduce per step: the gradient of the global batch (data parallel).
+Other workloads: fcc1m (1,048,576-atom FCC box, 64 radial + 16 x 8 angular, 192-128-64-1, BF16),
+water32k (32,768-atom O/H box, rc 6, 256-256-128-1, BF16), diamond64 (64-atom diamond cell,
+96-256-128-32-1, FP32), molecules1024 (the training step: loss and its parameter gradient over
+1024 molecules, FP32), stored / qeq / md (precomputed descriptors, charge equilibration,
+Langevin dynamics).
+
+Every line carries the roofline of the dominant kernel, the FP64 oracle timed on the host's
+cores as `cpu_baseline` (one core and all cores), `e2e` through the C ABI with host buffers,
+and, for the inference workloads, the force error against the oracle on a stated sample.
+--impl reference times the oracle itself (all host cores) on a bounded sample of the workload.
+Under torchrun every rank evaluates its own batch (seed + rank; weak scaling); the inference
+workloads need no collective, the training step sums its gradient with one all-reduce.
 """
 from __future__ import annotations
 
@@ -21,6 +30,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -32,9 +42,12 @@ if ROOT not in sys.path:
 
 METRIC = "energy+force atoms/sec at stated force error vs FP64; % HBM/tensor roofline"
 UNIT = "atoms/s"
-WORKLOAD = "molecules1024"
+INFER = ("ragged4096", "fcc1m", "water32k", "diamond64")
+TRAIN = "molecules1024"
+DEFAULT_WORKLOAD = "ragged4096"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 N_SM, FP32_LANES = 152, 128
+TOL_F = {"fp32": 1e-5, "bf16": 1e-2}   # max |dF| / RMS(F) against the FP64 oracle
 
 
 def workload_desc(wl):
@@ -45,6 +58,19 @@ def workload_desc(wl):
                                  "-".join(str(w) for w in wl.archs[0].widths), wl.w_force))
 
 
+INFER_DESC = {
+    "ragged4096": "4096 periodic cubic boxes, N log-uniform 32..4096 (%d atoms), 3 species (Dirichlet(1,1,1) "
+                  "proportions), 0.05 atoms/A^3, rc 5.5 A, D=480 (32 radial + 8x8 angular), networks "
+                  "480-128-32-1 per species; energies + forces",
+    "fcc1m": "periodic FCC box 64^3 cells (%d atoms), a=4.05 A, sigma 0.05 A, rc 5.0 A, D=192 (64 radial + "
+             "16 theta x 8 R), network 192-128-64-1; energies + forces",
+    "water32k": "periodic O/H box (%d atoms, O:H 1:2, 0.1003 atoms/A^3, min sep 0.9 A), rc 6.0 A, D=256, "
+                "networks 256-256-128-1 per species; energies + forces",
+    "diamond64": "periodic diamond cell 2x2x2 (%d atoms), a=5.43 A, sigma 0.1 A, rc 4.6 A, D=96, network "
+                 "96-256-128-32-1; energies + forces",
+}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -53,13 +79,11 @@ def dist_env():
 
 
 TRAFFIC_FILE = "profiles/geometry_kernels_molecules1024.md"
-
-
 STORE_TRAFFIC_FILE = "profiles/store_kernels_molecules1024.md"
 
 
 def measured_traffic(kernel, path=TRAFFIC_FILE):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when there is
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, or None when there is
     none or the kernel source has changed since the counters were taken."""
     import hashlib
     try:
@@ -84,6 +108,24 @@ def load_peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def host_info():
+    """Host cores available to this process and the CPU model (for the oracle baselines)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, "%s (%s)" % (model or platform.processor() or "unknown", platform.machine())
 
 
 # ------------------------------------------------------------------ clocks
@@ -133,7 +175,406 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ reference arm (oracle)
+# ------------------------------------------------------------------ the oracle on the host cores
+#
+# The oracle runs as it stands (FP64, one thread per call).  "All cores" runs independent
+# calls side by side in a process pool started with `spawn` (no process is forked after the
+# GPU is in use); the pool is warmed up first so that interpreter start-up is not timed.
+
+def _orc_batch_job(job):
+    """One oracle call in a worker: (system, desc, archs, theta) -> (atoms, seconds, E_cfg, F)."""
+    from oracle import oracle as O
+    system, desc, archs, theta = job
+    t0 = time.perf_counter()
+    r = O.batch(system, desc, archs, theta)
+    return system.n_atoms, time.perf_counter() - t0, r["E_cfg"], r["F"]
+
+
+def _orc_sampled_job(job):
+    from oracle import oracle as O
+    system, cfg, desc, archs, theta, samples = job
+    r = O.sampled(system, cfg, desc, archs, theta, samples)
+    return samples, r["F"], r["E"]
+
+
+def _orc_ping(_):
+    from oracle import oracle as O
+    O.lib()
+    return os.getpid()
+
+
+class OraclePool:
+    def __init__(self, workers: int):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.workers = workers
+        self.ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+        list(self.ex.map(_orc_ping, range(4 * workers)))
+
+    def map(self, fn, jobs):
+        return list(self.ex.map(fn, jobs))
+
+    def close(self):
+        self.ex.shutdown(wait=True)
+
+
+def oracle_samples(name, wl, seed):
+    """The bounded samples the oracle runs on, per workload: (one-core jobs, all-core jobs,
+    description).  Each job is one oracle call (system, desc, archs, theta)."""
+    import numpy as np
+    from paper_2305_11805_gb300 import workloads as W
+    th = wl.theta.astype(np.float32).astype(np.float64)
+    if name == "ragged4096":
+        jobs = [(wl.system.subset([c]), wl.desc, wl.archs, th) for c in range(64)]
+        return jobs, jobs, "configurations 0..63 of the batch (%d atoms)" % sum(j[0].n_atoms for j in jobs)
+    if name in ("fcc1m", "water32k", "diamond64"):
+        mk = {"fcc1m": lambda s: W.fcc(s, 8), "water32k": lambda s: W.water(s, 512),
+              "diamond64": lambda s: W.diamond64(s)}[name]
+        subs = [mk(seed + 1000 + k) for k in range(64)]
+        jobs = [(b.system, wl.desc, wl.archs, th) for b in subs]
+        what = {"fcc1m": "periodic FCC boxes of 8^3 cells (2048 atoms) with the fcc1m recipe, descriptor and "
+                         "network, other seeds",
+                "water32k": "periodic 512-atom boxes with the water32k recipe, descriptor and network, other seeds",
+                "diamond64": "64-atom diamond cells (other seeds)"}[name]
+        return jobs, jobs, what
+    raise ValueError(name)
+
+
+def cpu_baseline(name, wl, seed, seconds, pool):
+    """The oracle timed on one core (calls in turn until `seconds` have passed) and on all cores
+    (as many calls as workers x rounds, side by side).  Returns the baseline record and the
+    oracle results of the all-core run (for the force error of the GPU result)."""
+    one, many, what = oracle_samples(name, wl, seed)
+    cores, model = host_info()
+    atoms1, t1, k = 0, 0.0, 0
+    while k < len(one) and (t1 < seconds or k == 0):
+        n, dt, _, _ = _orc_batch_job(one[k])
+        atoms1 += n
+        t1 += dt
+        k += 1
+    v1 = atoms1 / t1
+    res, v_all, n_all, t_all = None, None, 0, None
+    if pool is not None:
+        # about `seconds` of wall time on all workers, whole rounds of calls
+        per_call = t1 / k
+        n_calls = max(pool.workers, min(len(many), int(pool.workers * seconds / max(per_call, 1e-3))))
+        n_calls = min(len(many), n_calls)
+        t0 = time.perf_counter()
+        res = pool.map(_orc_batch_job, many[:n_calls])
+        t_all = time.perf_counter() - t0
+        n_all = sum(r[0] for r in res)
+        v_all = n_all / t_all
+    rec = {"value": v_all if v_all else v1, "unit": UNIT, "cores": pool.workers if pool else 1, "kind": "oracle",
+           "sample": "%s; energies + forces, FP64" % what,
+           "one_core": {"value": v1, "calls": k, "atoms": atoms1, "seconds": round(t1, 2)},
+           "all_cores": None if pool is None else {"value": v_all, "cores": pool.workers, "calls": len(res),
+                                                   "atoms": n_all, "seconds": round(t_all, 2)},
+           "nproc": cores, "cpu_model": model}
+    return rec, (many[:len(res)] if res else []), res
+
+
+def force_error(F, Fo):
+    """max |F - Fo| / RMS(Fo) (the tolerance of the FP32 and BF16 paths)."""
+    import numpy as np
+    rms = float(np.sqrt((Fo ** 2).mean()))
+    return float(np.abs(F - Fo).max() / rms) if rms > 0 else float(np.abs(F - Fo).max())
+
+
+def force_error_sample(name, wl, F_gpu, E_gpu, pool, base_res, base_jobs, seed):
+    """Force (and energy) error of the GPU result against the oracle on a stated sample of the
+    same batch: whole configurations of the ragged batch (the ones the all-core baseline ran),
+    sampled atoms of the big boxes (the oracle evaluates each one by brute force)."""
+    import numpy as np
+    s = wl.system
+    th = wl.theta.astype(np.float32).astype(np.float64)
+    if name == "ragged4096":
+        n_cfg = len(base_res)
+        a1 = int(s.atom_off[n_cfg])
+        Fo = np.concatenate([r[3] for r in base_res])
+        Eo = np.concatenate([r[2] for r in base_res])
+        ferr = force_error(F_gpu[:a1], Fo)
+        eerr = float(np.max(np.abs(E_gpu[:n_cfg] - Eo) / np.maximum(np.abs(Eo), 1e-30)))
+        return {"max_abs_over_rms": ferr, "energy_rel": eerr, "sample": "configurations 0..%d (%d atoms), "
+                "whole-configuration FP64 oracle" % (n_cfg - 1, a1)}
+    if name == "diamond64":
+        r = base_res[0]
+        return {"max_abs_over_rms": force_error(F_gpu, r[3]),
+                "energy_rel": float(abs(E_gpu[0] - r[2][0]) / abs(r[2][0])),
+                "sample": "the whole 64-atom cell, FP64 oracle"}
+    rng = np.random.default_rng(seed + 17)
+    n_smp = 32
+    smp = sorted(rng.choice(s.n_atoms, n_smp, replace=False).tolist())
+    per = max(1, n_smp // (pool.workers if pool else 1))
+    jobs = [(s, 0, wl.desc, wl.archs, th, smp[k:k + per]) for k in range(0, n_smp, per)]
+    out = pool.map(_orc_sampled_job, jobs) if pool else [_orc_sampled_job(j) for j in jobs]
+    idx = np.concatenate([np.asarray(o[0]) for o in out])
+    Fo = np.concatenate([o[1] for o in out])
+    rms = float(np.sqrt((F_gpu.astype(np.float64) ** 2).mean()))
+    ferr = float(np.abs(F_gpu[idx] - Fo).max() / rms)
+    return {"max_abs_over_rms": ferr, "sample": "%d random atoms of the box, each evaluated by the FP64 oracle "
+            "(brute force over its environment); RMS over all atoms of the GPU result" % n_smp}
+
+
+def run_infer(args):
+    """Energies and forces of one inference workload, the whole pass as one captured CUDA graph."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    name = args.workload
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2305_11805_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2305_11805_gb300 import panna as P
+    from paper_2305_11805_gb300 import workloads as W
+    # the oracle pool first (spawned workers; no fork after the GPU is in use)
+    pool = None
+    if rank == 0 and args.cpu_seconds > 0:
+        from oracle import oracle as O
+        O.build()
+        pool = OraclePool(max(1, min(host_info()[0], 64)))
+
+    wl = W.make(name, seed=args.seed + rank)
+    s = wl.system
+    N, C = s.n_atoms, s.n_cfg
+    dev = torch.device("cuda", local)
+    bf16 = bool(wl.mlp_bf16)
+    prec = P.PANNA_MLP_BF16 if bf16 else P.PANNA_MLP_FP32
+    pot = P.Potential(wl.desc, wl.archs)
+    sysd = P.DeviceSystem(wl.system)
+    theta = torch.as_tensor(wl.theta.astype(np.float32), device=dev)
+    E = torch.empty(C, dtype=torch.float64, device=dev)
+    F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    small = N * wl.desc.D * 4 < 512 * 1024 * 1024     # descriptor rows alone below 4 x L2: flush
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if small else None
+
+    fp32_tflops, ex2_gops = P.panna_measure_alu_peaks()
+
+    # stage times of the same call (direct calls with stage events; the graph has none)
+    P.panna_energy_forces(pot.ctx, sysd, theta, prec, E, None, F, None)
+    P.panna_set_profiling(pot.ctx, True)
+    stages = ["neighbors", "descriptor", "mlp", "adjoint", "forces"]
+    stage_ms = {k: 0.0 for k in stages}
+    n_prof = 3
+    for _ in range(n_prof):
+        if flush is not None:
+            flush.fill_(1.0)
+        P.panna_energy_forces(pot.ctx, sysd, theta, prec, E, None, F, None)
+        for k in stages:
+            v = P.panna_stage_ms(pot.ctx, k)
+            if v > 0:
+                stage_ms[k] += v / n_prof
+    P.panna_set_profiling(pot.ctx, False)
+
+    # ---- device-timed region: the captured graph, inputs resident in HBM
+    P.panna_capture(pot.ctx, sysd, theta, prec, E, None, F, None)
+    launches = P.panna_last_launch_count(pot.ctx)
+    for _ in range(args.warmup):
+        P.panna_replay(pot.ctx, stream)
+    P.panna_check(pot.ctx, stream)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        if flush is not None:
+            flush.fill_(float(k))
+        starts[k].record(stream)
+        P.panna_replay(pot.ctx, stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    P.panna_check(pot.ctx, stream)
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    ms_per_step = t_ms / args.steps
+    value = world * N * args.steps / (t_ms * 1e-3)
+    F_host = F.cpu().numpy().astype(np.float64)
+    E_host = E.cpu().numpy()
+
+    # ---- end to end through the C ABI with host buffers: inputs copied from pinned host memory
+    # into the arrays the graph reads, the graph replayed, energies and forces read back
+    hs = [torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+          for a in (s.atom_off, s.pos, s.species.astype(np.int32), s.cell, s.pbc.astype(np.uint8))]
+    ds = [sysd.atom_off, sysd.pos, sysd.species, sysd.cell, sysd.pbc]
+    hE = torch.empty(C, dtype=torch.float64).pin_memory()
+    hF = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in hs)
+    d2h = hE.numel() * 8 + hF.numel() * 4
+
+    def e2e_step():
+        for h, d in zip(hs, ds):
+            d.copy_(h, non_blocking=True)
+        P.panna_replay(pot.ctx, stream)
+        hE.copy_(E, non_blocking=True)
+        hF.copy_(F, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    P.panna_check(pot.ctx, stream)
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * N * args.steps / e2e_s
+
+    # ---- the plain FP32 path on one configuration per call (ragged batch): the comparison the
+    # batched BF16 graph is measured against, each with its force error
+    comparison = None
+    if name == "ragged4096" and rank == 0 and args.compare:
+        comparison = compare_single(args, P, wl, pot, sysd, theta, dev)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return 0
+
+    # ---- roofline of the dominant kernel: the descriptor and adjoint stages are one kernel
+    # launch each, bound by the FP32 pipe (hundreds of operations per byte); algorithmic FLOPs
+    # per unit are minimal operation counts (geometry, the zeta powers by repeated
+    # multiplication, the Gaussians, the outer product per pair of an 8 x 8 tile)
+    peaks, peak_kind = load_peaks()
+    off, _, _ = pot.neighbors(sysd)
+    nb = torch.diff(off).double()
+    n_entries = float(nb.sum().item())
+    n_pairs = float((nb * (nb - 1) / 2).sum().item())
+    d = wl.desc
+    nbins = d.n_theta * d.n_ang_r
+    per_pair = {"descriptor": 265.0 * nbins / 64, "adjoint": 495.0 * nbins / 64}
+    per_entry = {"descriptor": 6.0 * d.n_rad, "adjoint": 8.0 * d.n_rad}
+    stage_flops = {k: per_pair[k] * n_pairs + per_entry[k] * n_entries for k in per_pair}
+    counts = [int((s.species == q).sum()) for q in range(d.n_species)]
+    mlp_fwd = sum(2 * counts[q] * sum(a.widths[l] * a.widths[l + 1] for l in range(a.n_layers))
+                  for q, a in enumerate(wl.archs))
+    stage_flops["mlp"] = 2 * mlp_fwd      # forward + input gradient (algorithmic, one product each)
+    dom = max(("descriptor", "adjoint"), key=lambda k: stage_ms.get(k, 0.0))
+    ach = stage_flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_tflops, "unit": "TFLOP/s",
+            "frac": ach / fp32_tflops, "traffic": None,
+            "peak_source": "measured in this run: FP32 FMA microbenchmark (panna_measure_alu_peaks) on all SMs",
+            "derived_peak": N_SM * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12,
+            "ex2_peak_gops": ex2_gops, "ms_per_launch": stage_ms[dom],
+            "flop_per_angular_pair": per_pair[dom], "angular_pairs": n_pairs, "neighbour_entries": n_entries,
+            "stage_tflops": {k: round(stage_flops[k] / (stage_ms[k] * 1e-3) / 1e12, 3)
+                             for k in stage_flops if stage_ms.get(k, 0) > 0},
+            "mlp_tensor_frac_of_bf16_peak": (stage_flops["mlp"] / (stage_ms["mlp"] * 1e-3) / 1e12 /
+                                             peaks["bf16_tflops"]) if stage_ms.get("mlp", 0) > 0 else None}
+
+    cpu, base_jobs, base_res = (None, [], [])
+    ferr = None
+    if args.cpu_seconds > 0:
+        cpu, base_jobs, base_res = cpu_baseline(name, wl, args.seed, args.cpu_seconds, pool)
+        ferr = force_error_sample(name, wl, F_host, E_host, pool, base_res, base_jobs, args.seed)
+        ferr["precision"] = "bf16" if bf16 else "fp32"
+        ferr["bar"] = TOL_F["bf16" if bf16 else "fp32"]
+        if comparison is not None:
+            comparison["batched_bf16_graph"]["force_error"] = ferr["max_abs_over_rms"]
+            comparison["fp32_one_config_per_call"]["force_error"] = force_error(
+                comparison.pop("_F32")[:int(s.atom_off[len(base_res)])],
+                np.concatenate([r[3] for r in base_res]))
+        pool.close()
+    elif comparison is not None:
+        comparison.pop("_F32", None)
+    dtype = ("bf16 networks (hi+lo operands, FP32 accumulation); fp32 descriptors and adjoint; fp64 sums"
+             if bf16 else "fp32 (extended-precision angular terms); fp64 sums")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+           "config": {"workload": name + ": " + (INFER_DESC[name] % N), "atoms_per_gpu": N, "configs_per_gpu": C,
+                      "parallelism": "independent batches per rank (dp%d)" % world,
+                      "mode": "one captured CUDA graph per step (panna_capture / panna_replay)",
+                      "l2": "flushed between steps (256 MiB write)" if small else
+                            "working set (GBs) far larger than L2, no flush",
+                      "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()}},
+           "force_error": ferr, "roofline": roof, "cpu_baseline": cpu,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+           "gpu_launches": launches * args.steps, "clocks": clk}
+    if comparison is not None:
+        comparison["batched_bf16_graph"]["atoms_per_s"] = value
+        comparison["batched_bf16_graph"]["precision"] = "bf16 networks (hi+lo), fp32 descriptors"
+        comparison["speedup_batched_bf16_over_fp32_one_config_per_call"] = (
+            value / comparison["fp32_one_config_per_call"]["atoms_per_s"])
+        out["comparison"] = comparison
+    print(json.dumps(out))
+    if world > 1:
+        torch.distributed.barrier()
+    return 0
+
+
+def compare_single(args, P, wl, pot, sysd, theta, dev):
+    """The same batch through the plain FP32 path, one configuration per call (synchronous
+    panna_energy_forces per configuration), and the FP32 networks as one batched graph."""
+    import numpy as np
+    import torch
+    s = wl.system
+    N, C = s.n_atoms, s.n_cfg
+    stream = torch.cuda.current_stream()
+    off = torch.zeros((C, 2), dtype=torch.int64, device=dev)
+    off[:, 1] = torch.as_tensor(np.diff(s.atom_off), device=dev)
+    views = []
+    for c in range(C):
+        a0, a1 = int(s.atom_off[c]), int(s.atom_off[c + 1])
+        views.append(P.DeviceSystem.from_tensors(off[c], sysd.pos[a0:a1], sysd.species[a0:a1], sysd.cell[c:c + 1],
+                                                 sysd.pbc[c:c + 1]))
+    pot1 = P.Potential(wl.desc, wl.archs)
+    P.panna_set_tuning(pot1.ctx, "autotune", 0)   # no per-size measurement inside the loop
+    E1 = torch.empty(1, dtype=torch.float64, device=dev)
+    F32 = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    big = int(np.argmax(np.diff(s.atom_off)))
+    for v in [views[big]] + views[:16]:
+        P.panna_energy_forces(pot1.ctx, v, theta, P.PANNA_MLP_FP32, E1, None, F32[:v.n_atoms], None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, v in enumerate(views):
+        a0 = int(s.atom_off[c])
+        P.panna_energy_forces(pot1.ctx, v, theta, P.PANNA_MLP_FP32, E1, None, F32[a0:a0 + v.n_atoms], None)
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    pot1.close()
+    # FP32 networks, whole batch in one graph (separates batching from precision)
+    potb = P.Potential(wl.desc, wl.archs)
+    Eb = torch.empty(C, dtype=torch.float64, device=dev)
+    Fb = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    P.panna_capture(potb.ctx, sysd, theta, P.PANNA_MLP_FP32, Eb, None, Fb, None)
+    for _ in range(2):
+        P.panna_replay(potb.ctx, stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(3):
+        P.panna_replay(potb.ctx, stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    P.panna_check(potb.ctx, stream)
+    t_b32 = ev[0].elapsed_time(ev[1]) / 3
+    potb.close()
+    return {"fp32_one_config_per_call": {"atoms_per_s": N / t_one, "seconds": t_one,
+                                         "calls": C, "precision": "fp32 networks, extended angular terms"},
+            "fp32_batched_graph": {"atoms_per_s": N / (t_b32 * 1e-3), "ms": t_b32},
+            "batched_bf16_graph": {"atoms_per_s": None},
+            "_F32": F32.cpu().numpy().astype(np.float64)}
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
 
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -142,76 +583,131 @@ def run_reference(args):
     import numpy as np
     from oracle import oracle as O
     from paper_2305_11805_gb300 import workloads as W
-    wl = W.make(WORKLOAD, seed=args.seed)
-    n_mol = args.ref_molecules
-    sub = wl.system.subset(range(n_mol))
-    er = wl.e_ref[:n_mol]
-    fr = wl.f_ref[:sub.n_atoms]
-    th = wl.theta.astype(np.float32).astype(np.float64)
+    O.build()
+    name = args.workload
+    cores, model = host_info()
+    if name == TRAIN:
+        wl = W.make(TRAIN, seed=args.seed)
+        n_mol = args.ref_molecules
+        th = wl.theta.astype(np.float32).astype(np.float64)
+        sub = wl.system.subset(range(n_mol))
 
-    def step():
-        O.batch(sub, wl.desc, wl.archs, th, e_ref=er, f_ref=fr, w_force=wl.w_force, param_grad=True)
+        def step():
+            O.batch(sub, wl.desc, wl.archs, th, e_ref=wl.e_ref[:n_mol], f_ref=wl.f_ref[:sub.n_atoms],
+                    w_force=wl.w_force, param_grad=True)
+        atoms = sub.n_atoms
+        used = 1
+        sample = "first %d of the 1024 molecules (%d atoms), full training step, FP64 oracle, 1 thread" % (
+            n_mol, atoms)
+        cfg = workload_desc(wl)
+        dtype = "f64"
+    elif name in INFER:
+        wl = W.make(name, seed=args.seed)
+        one, many, what = oracle_samples(name, wl, args.seed)
+        pool = OraclePool(max(1, min(cores, 64)))
+        used = pool.workers
+        n_calls = {"ragged4096": 32, "fcc1m": used, "water32k": used, "diamond64": 4 * used}[name]
+        jobs = many[:n_calls]
+        atoms = sum(j[0].n_atoms for j in jobs)
 
+        def step():
+            pool.map(_orc_batch_job, jobs)
+        sample = "%d oracle calls side by side on %d host cores: %s; %d atoms per step" % (
+            len(jobs), used, what if name != "ragged4096" else "configurations 0..%d of the batch" % (n_calls - 1),
+            atoms)
+        cfg = name + ": " + (INFER_DESC[name] % wl.system.n_atoms)
+        dtype = "f64"
+    else:
+        print(json.dumps({"impl": "reference", "unavailable": "no oracle arm for workload %s" % name}))
+        return 0
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
     dt = time.perf_counter() - t0
-    v = sub.n_atoms * args.steps / dt
-    sample = "first %d of the 1024 molecules (%d atoms), full training step, FP64 oracle, 1 thread" % (
-        n_mol, sub.n_atoms)
+    if name in INFER:
+        pool.close()
+    v = atoms * args.steps / dt
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": workload_desc(wl), "sample": sample},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+           "data": "synthetic", "config": {"workload": cfg, "sample": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                            "nproc": cores, "cpu_model": model},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
 
 
-def cpu_baseline(wl, seconds: float):
-    """The oracle as it stands, single thread, on batches of 32 molecules until ~seconds."""
-    import numpy as np
-    from oracle import oracle as O
-    th = wl.theta.astype(np.float32).astype(np.float64)
-    atoms, t0, k = 0, time.perf_counter(), 0
-    while True:
-        cfgs = range(32 * k, 32 * (k + 1))
-        sub = wl.system.subset(cfgs)
-        O.batch(sub, wl.desc, wl.archs, th, e_ref=wl.e_ref[32 * k:32 * (k + 1)],
-                f_ref=wl.f_ref[int(wl.system.atom_off[32 * k]):int(wl.system.atom_off[32 * (k + 1)])],
-                w_force=wl.w_force, param_grad=True)
-        atoms += sub.n_atoms
-        k += 1
-        dt = time.perf_counter() - t0
-        if dt >= seconds or 32 * (k + 1) > wl.system.n_cfg:
-            break
-    return {"value": atoms / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "training step on the first %d molecules (%d atoms) in batches of 32, %.1f s, "
-                      "FP64, 1 thread" % (32 * k, atoms, dt)}
 
+def _orc_train_job(job):
+    """One training-step oracle call in a worker: (system, desc, archs, theta, e_ref, f_ref, w_force)."""
+    from oracle import oracle as O
+    system, desc, archs, theta, er, fr, wf = job
+    t0 = time.perf_counter()
+    O.batch(system, desc, archs, theta, e_ref=er, f_ref=fr, w_force=wf, param_grad=True)
+    return system.n_atoms, time.perf_counter() - t0
+
+
+def cpu_baseline_train(wl, seconds, pool):
+    """The oracle's training step (loss and parameter gradient) on batches of 32 molecules: one
+    core (batches in turn until `seconds` have passed) and all cores (batches side by side)."""
+    import numpy as np
+    th = wl.theta.astype(np.float32).astype(np.float64)
+    s = wl.system
+    jobs = []
+    for k in range(s.n_cfg // 32):
+        a0, a1 = int(s.atom_off[32 * k]), int(s.atom_off[32 * (k + 1)])
+        jobs.append((s.subset(range(32 * k, 32 * (k + 1))), wl.desc, wl.archs, th, wl.e_ref[32 * k:32 * (k + 1)],
+                     wl.f_ref[a0:a1], wl.w_force))
+    cores, model = host_info()
+    atoms1, t1, k = 0, 0.0, 0
+    while k < len(jobs) and (t1 < seconds or k == 0):
+        n, dt = _orc_train_job(jobs[k])
+        atoms1 += n
+        t1 += dt
+        k += 1
+    rec = {"value": atoms1 / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "training step (loss + parameter gradient) on batches of 32 molecules, FP64",
+           "one_core": {"value": atoms1 / t1, "calls": k, "atoms": atoms1, "seconds": round(t1, 2)},
+           "all_cores": None, "nproc": cores, "cpu_model": model}
+    if pool is not None:
+        n_calls = min(len(jobs), max(pool.workers, int(pool.workers * seconds / max(t1 / k, 1e-3))))
+        t0 = time.perf_counter()
+        res = pool.map(_orc_train_job, jobs[:n_calls])
+        ta = time.perf_counter() - t0
+        na = sum(r[0] for r in res)
+        rec["all_cores"] = {"value": na / ta, "cores": pool.workers, "calls": n_calls, "atoms": na,
+                            "seconds": round(ta, 2)}
+        rec["value"] = na / ta
+        rec["cores"] = pool.workers
+    return rec
 
 # ------------------------------------------------------------------ our arm
 
-def run_ours(args):
+def run_training(args):
     import numpy as np
     import torch
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    pool = None
+    if rank == 0 and args.cpu_seconds > 0:
+        from oracle import oracle as O
+        O.build()
+        pool = OraclePool(max(1, min(host_info()[0], 64)))
     torch.cuda.set_device(local)
     from paper_2305_11805_gb300 import build
-    if rank == 0 and not os.path.exists(build.LIB):
+    if rank == 0:
         build.build()
     if world > 1:
         dist.barrier()
     from paper_2305_11805_gb300 import panna as P
     from paper_2305_11805_gb300 import workloads as W
 
-    wl = W.make(WORKLOAD, seed=args.seed + rank)
+    wl = W.make(TRAIN, seed=args.seed + rank)
     N, C = wl.system.n_atoms, wl.system.n_cfg
     dev = torch.device("cuda", local)
     pot = P.Potential(wl.desc, wl.archs)
@@ -315,6 +811,8 @@ def run_ours(args):
             torch.distributed.barrier()
         return 0
 
+    fp32_tflops, ex2_gops = P.panna_measure_alu_peaks()
+
     # ---- roofline of the dominant kernel.  The descriptor, adjoint and JVP stages are one
     # kernel launch each (FP32 CUDA-core arithmetic, "alu"); algorithmic FLOPs per unit are
     # minimal operation counts (geometry, 8 zeta-powers by 7 multiplies, 8 Gaussians, the
@@ -344,16 +842,18 @@ def run_ours(args):
         dom = max(kernels, key=per_step.get)
         ach = stage_flops[dom] / (per_step[dom] * 1e-3) / 1e12
         traffic = measured_traffic(dom)
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)" % (
-                    clock_mhz, peak_kind),
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_tflops,
+                "unit": "TFLOP/s", "frac": ach / fp32_tflops, "traffic": traffic,
+                "peak_source": "measured in this run: FP32 FMA microbenchmark (panna_measure_alu_peaks) on all SMs",
+                "derived_peak": alu_peak, "ex2_peak_gops": ex2_gops,
                 "ms_per_launch": per_step[dom],
                 "traffic_source": TRAFFIC_FILE if traffic is not None else None,
                 "all_stages_tflops": {s: round(stage_flops[s] / (per_step[s] * 1e-3) / 1e12, 2)
                                       for s in stage_flops if per_step.get(s, 0) > 0},
                 "pairs_per_step": n_pairs, "neighbour_entries_per_step": n_entries}
-    cpu = cpu_baseline(wl, args.cpu_seconds) if args.cpu_seconds > 0 else None
+    cpu = cpu_baseline_train(wl, args.cpu_seconds, pool) if args.cpu_seconds > 0 else None
+    if pool is not None:
+        pool.close()
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
@@ -369,80 +869,6 @@ def run_ours(args):
     return 0
 
 
-def run_ragged(args):
-    """Ragged batch of 4096 periodic boxes (32..4096 atoms), BF16 networks: the whole batch as
-    one captured CUDA graph versus the same configurations launched one call at a time."""
-    import numpy as np
-    import torch
-    from paper_2305_11805_gb300 import build
-    build.build()
-    from paper_2305_11805_gb300 import panna as P
-    from paper_2305_11805_gb300 import workloads as W
-    torch.cuda.set_device(dist_env()[2])
-    wl = W.make("ragged4096", seed=args.seed)
-    s = wl.system
-    N, C = s.n_atoms, s.n_cfg
-    pot = P.Potential(wl.desc, wl.archs)
-    sysd = P.DeviceSystem(s)
-    theta = torch.as_tensor(wl.theta.astype(np.float32), device="cuda")
-    prec = P.PANNA_MLP_BF16
-    E = torch.empty(C, dtype=torch.float64, device="cuda")
-    Ea = torch.empty(N, dtype=torch.float32, device="cuda")
-    F = torch.empty((N, 3), dtype=torch.float32, device="cuda")
-    V = torch.empty((C, 3, 3), dtype=torch.float64, device="cuda")
-    P.panna_capture(pot.ctx, sysd, theta, prec, E, Ea, F, V)
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        P.panna_replay(pot.ctx, stream)
-    P.panna_check(pot.ctx, stream)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    clocks = ClockSampler(0)
-    clocks.start()
-    time.sleep(0.3)
-    ev[0].record(stream)
-    for _ in range(args.steps):
-        P.panna_replay(pot.ctx, stream)
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    P.panna_check(pot.ctx, stream)
-    t_graph = ev[0].elapsed_time(ev[1]) / args.steps
-    # the same configurations, one call each
-    off = torch.zeros((C, 2), dtype=torch.int64, device="cuda")
-    off[:, 1] = torch.as_tensor(np.diff(s.atom_off), device="cuda")
-    pot1 = P.Potential(wl.desc, wl.archs)
-    views = []
-    for c in range(C):
-        a0 = int(s.atom_off[c])
-        views.append(P.DeviceSystem.from_tensors(off[c], sysd.pos[a0:int(s.atom_off[c + 1])],
-                                                 sysd.species[a0:int(s.atom_off[c + 1])], sysd.cell[c:c + 1],
-                                                 sysd.pbc[c:c + 1]))
-    out1 = [torch.empty(1, dtype=torch.float64, device="cuda"), None]
-    P.panna_set_tuning(pot1.ctx, "autotune", 0)   # no per-size measurement inside the loop
-    big = int(np.argmax(np.diff(s.atom_off)))
-    for v in [views[big]] + views[:16]:
-        n = v.n_atoms
-        P.panna_energy_forces(pot1.ctx, v, theta, prec, out1[0], None, F[:n], None)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for v in views:
-        P.panna_energy_forces(pot1.ctx, v, theta, prec, out1[0], None, F[:v.n_atoms], None)
-    torch.cuda.synchronize()
-    t_one = time.perf_counter() - t0
-    out = {"metric": METRIC, "value": N / (t_graph * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": t_graph, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "bf16 (hi+lo operands), fp32 descriptors", "data": "synthetic",
-           "config": {"workload": "4096 periodic cubic boxes, N log-uniform 32..4096 (%d atoms), 3 species, "
-                                  "0.05 atoms/A^3, rc 5.5, D=480, networks 480-128-32-1, energy+forces" % N,
-                      "mode": "one captured CUDA graph per step (replay)",
-                      "one_config_per_call_atoms_per_s": N / t_one,
-                      "one_config_per_call_s": t_one,
-                      "graph_kernels_per_replay": P.panna_last_launch_count(pot.ctx),
-                      "l2": "working set (several GB) larger than L2"},
-           "clocks": clk}
-    print(json.dumps(out))
-    return 0
-
 
 def run_stored(args):
     """The same training step (molecules1024) from precomputed descriptors with stored
@@ -457,7 +883,7 @@ def run_stored(args):
     from paper_2305_11805_gb300 import panna as P
     from paper_2305_11805_gb300 import workloads as W
     torch.cuda.set_device(dist_env()[2])
-    wl = W.make(WORKLOAD, seed=args.seed)
+    wl = W.make(TRAIN, seed=args.seed)
     N, C = wl.system.n_atoms, wl.system.n_cfg
     pot = P.Potential(wl.desc, wl.archs)
     sysd = P.DeviceSystem(wl.system)
@@ -731,6 +1157,7 @@ def run_md(args):
     return 0
 
 
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -738,29 +1165,26 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-molecules", type=int, default=24)
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "ragged4096", "md", "stored", "qeq"])
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the FP32 one-configuration-per-call comparison (ragged4096)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(INFER) + [TRAIN, "md", "stored", "qeq"])
     args = ap.parse_args()
-    if args.workload != WORKLOAD and args.impl == "ours":
-        # the secondary workloads are single-GPU measurements: under torchrun rank 0 runs on
-        # its own device and prints the line, the other ranks exit without work
-        rank, world, local = dist_env()
-        if rank != 0:
-            return 0
-        import torch
-        torch.cuda.set_device(local)
-    if args.workload == "ragged4096" and args.impl == "ours":
-        return run_ragged(args)
-    if args.workload == "md" and args.impl == "ours":
-        return run_md(args)
-    if args.workload == "stored" and args.impl == "ours":
-        return run_stored(args)
-    if args.workload == "qeq" and args.impl == "ours":
-        return run_qeq(args)
     if args.impl == "reference":
         return run_reference(args)
-    return run_ours(args)
+    if args.workload in INFER:
+        return run_infer(args)
+    if args.workload == TRAIN:
+        return run_training(args)
+    # the remaining workloads are single-GPU measurements: under torchrun rank 0 runs on its
+    # own device and prints the line, the other ranks exit without work
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    return {"md": run_md, "stored": run_stored, "qeq": run_qeq}[args.workload](args)
 
 
 if __name__ == "__main__":

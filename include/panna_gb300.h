@@ -559,6 +559,18 @@ panna_status panna_set_profiling(panna_ctx* ctx, int32_t on);
 float panna_stage_ms(const panna_ctx* ctx, const char* stage);
 
 /*
+ * Measured throughput of the arithmetic units that bound the descriptor, adjoint and JVP
+ * kernels (they perform hundreds of FP32 operations per byte they move, so their roofline is
+ * an arithmetic one, not HBM): *fp32_tflops (host) = FP32 FMA throughput in TFLOP/s (an FMA
+ * counts as two operations), *ex2_gops (host) = multi-function-unit ex2 results per second in
+ * units of 1e9.  Microbenchmark kernels with independent dependency chains on every SM, timed
+ * with CUDA events on `stream` (best of three launches after a warm-up, about 0.2 s in all),
+ * at whatever clocks the GPU runs at the time.  Allocates and frees a few kB (stream-ordered).
+ * The paper has no counterpart: this is the denominator of the kernels' reported efficiency.
+ */
+panna_status panna_measure_alu_peaks(double* fp32_tflops, double* ex2_gops, panna_stream_t stream);
+
+/*
  * Descriptors G [n_atoms*D] FP32 (device, row i = atom i) of a small batch, computed
  * without allocating any memory: no context, no cudaMalloc, no cudaFree.  The paper has
  * no counterpart; this entry point exists for callers that cannot allocate device memory

@@ -654,8 +654,10 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
     k_set_cell_base<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(w.geom, w.cell_start, C);
     ++*launches;
     // total cells <= 2N + C by construction; clear the counters
-    cudaMemsetAsync(w.cell_count, 0, sizeof(int64_t) * (w.cap_cells + 1), s);
-    cudaMemsetAsync(w.cell_fill, 0, sizeof(int32_t) * w.cap_cells, s);
+    e = cudaMemsetAsync(w.cell_count, 0, sizeof(int64_t) * (w.cap_cells + 1), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(w.cell_fill, 0, sizeof(int32_t) * w.cap_cells, s);
+    if (e != cudaSuccess) return e;
     k_bin<<<nbA, 256, 0, s>>>(sys, d.S, w.geom, w.atom_cfg, w.atom_cell, w.cell_count, w.pos_hi, w.pos_lo,
                               w.wrap, w.status);
     ++*launches;

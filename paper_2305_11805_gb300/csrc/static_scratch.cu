@@ -88,7 +88,7 @@ extern "C" panna_status panna_descriptors_static(const panna_desc_params* p, con
     if (!p || !sys || !G) return sfail(PANNA_ERR_INVALID_ARG, "null argument");
     bool unsupported = false;
     if (const char* why = desc_params_check(p, &unsupported))
-        return sfail(PANNA_ERR_INVALID_ARG, why);
+        return sfail(unsupported ? PANNA_ERR_UNSUPPORTED : PANNA_ERR_INVALID_ARG, why);
     const int64_t N = sys->n_atoms, C = sys->n_cfg;
     if (C < 1 || N < 0 || !sys->atom_off || !sys->cell || !sys->pbc || (N > 0 && (!sys->pos || !sys->species)))
         return sfail(PANNA_ERR_INVALID_ARG, "invalid system");
@@ -134,35 +134,27 @@ extern "C" panna_status panna_descriptors_static(const panna_desc_params* p, con
     DescDev d{};
     desc_dev_from_params(p, d);
 
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        carve_static(base, N, C, (int)cap, w);
-        w.sys = sys;
-        int launches = 0;
-        // the array keeps the previous call's contents: clear what must start at zero
-        cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s);
-        if (e == cudaSuccess) e = build_neighbors(w, d, s, &launches);
-        if (e == cudaSuccess) e = launch_descriptor(w, d, G, nullptr, true, s, &launches);
-        DevStatus h{};
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, w.status, sizeof h, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            snprintf(msg, sizeof msg, "CUDA error: %s", cudaGetErrorString(e));
-            return sfail(PANNA_ERR_CUDA, msg);
-        }
-        if (h.code == 0) return PANNA_OK;
-        if (h.code == PANNA_ERR_NEIGHBOR_OVERFLOW && attempt == 0) {
-            // a larger capacity may still fit the array
-            const int64_t fit = N > 0 ? (int64_t)((kStaticScratchBytes - fixed - 1024) / ((size_t)N * per_slot)) : 0;
-            if (h.need_cap <= fit && h.need_cap <= kStaticMaxCap && h.need_cap > cap) {
-                cap = h.need_cap;
-                continue;
-            }
-            snprintf(msg, sizeof msg, "atom %d has %d neighbours; the static scratch holds %lld per atom for "
-                     "%lld atoms", h.bad_index, h.need_cap, (long long)cap, (long long)N);
-            return sfail(PANNA_ERR_NEIGHBOR_OVERFLOW, msg);
-        }
-        snprintf(msg, sizeof msg, "device error %d at index %d", h.code, h.bad_index);
-        return sfail((panna_status)h.code, msg);
+    // one pass at the largest capacity that fits: a larger one cannot exist
+    carve_static(base, N, C, (int)cap, w);
+    w.sys = sys;
+    int launches = 0;
+    // the array keeps the previous call's contents: clear what must start at zero
+    cudaError_t e = cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s);
+    if (e == cudaSuccess) e = build_neighbors(w, d, s, &launches);
+    if (e == cudaSuccess) e = launch_descriptor(w, d, G, nullptr, true, s, &launches);
+    DevStatus h{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, w.status, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof msg, "CUDA error: %s", cudaGetErrorString(e));
+        return sfail(PANNA_ERR_CUDA, msg);
     }
-    return PANNA_OK;
+    if (h.code == 0) return PANNA_OK;
+    if (h.code == PANNA_ERR_NEIGHBOR_OVERFLOW) {
+        snprintf(msg, sizeof msg, "atom %d has %d neighbours; the static scratch holds %lld per atom for "
+                 "%lld atoms", h.bad_index, h.need_cap, (long long)cap, (long long)N);
+        return sfail(PANNA_ERR_NEIGHBOR_OVERFLOW, msg);
+    }
+    snprintf(msg, sizeof msg, "device error %d at index %d", h.code, h.bad_index);
+    return sfail((panna_status)h.code, msg);
 }

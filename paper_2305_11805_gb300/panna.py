@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
         "panna_set_profiling": (i32, [_vp, i32]),
         "panna_stage_ms": (f32, [_vp, C.c_char_p]),
         "panna_descriptors_static": (i32, [C.POINTER(panna_desc_params), C.POINTER(panna_system), _vp, _vp]),
+        "panna_measure_alu_peaks": (i32, [C.POINTER(f64), C.POINTER(f64), _vp]),
         "panna_capture": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
         "panna_replay": (i32, [_vp, _vp]),
         "panna_set_qeq": (i32, [_vp, C.POINTER(panna_qeq_params)]),
@@ -156,7 +157,7 @@ def exported_symbols() -> Sequence[str]:
             "panna_md_run", "panna_set_loss_options", "panna_set_frozen", "panna_adam_step",
             "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
-            "panna_descriptors_static", "panna_capture", "panna_replay", "panna_store_plan",
+            "panna_descriptors_static", "panna_measure_alu_peaks", "panna_capture", "panna_replay", "panna_store_plan",
             "panna_store_sections", "panna_store_build", "panna_store_energy_forces", "panna_store_loss_grad",
             "panna_set_qeq", "panna_qeq_energy_forces", "panna_qeq_loss_grad"]
 
@@ -169,6 +170,26 @@ def _check(status: int):
 def _ptr(t) -> Optional[int]:
     if t is None:
         return None
+    return t.data_ptr()
+
+
+def _dev(t, dtype: str, numel: int, name: str):
+    """Pointer of a caller-owned device buffer after checking what the C ABI will assume of
+    it: a contiguous CUDA tensor of `dtype` (torch dtype name) on the current device holding
+    exactly `numel` elements.  The kernels write every element, so a smaller buffer would be
+    overwritten past its end."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if str(t.dtype) != "torch." + dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() != numel:
+        raise ValueError("%s must hold %d elements, got %d" % (name, numel, t.numel()))
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (
+            name, t.device.index, torch.cuda.current_device()))
     return t.data_ptr()
 
 
@@ -324,7 +345,18 @@ def panna_stage_ms(ctx: int, stage: str) -> float:
 def panna_descriptors_static(desc, sysd: "DeviceSystem", G, stream=None):
     """Descriptors into G without any device allocation (static scratch; see the header)."""
     h = _DescHolder(desc)
-    _check(load().panna_descriptors_static(C.byref(h.s), C.byref(sysd.s), _ptr(G), _stream(stream)))
+    D = int(load().panna_descriptor_size(C.byref(h.s)))
+    if D < 0:
+        raise PannaError(PANNA_ERR_INVALID_ARG, "invalid descriptor parameters")
+    gp = _dev(G, "float32", sysd.n_atoms * D, "G")
+    _check(load().panna_descriptors_static(C.byref(h.s), C.byref(sysd.s), gp, _stream(stream)))
+
+
+def panna_measure_alu_peaks(stream=None):
+    """(FP32 FMA TFLOP/s, ex2 G results/s) measured now on the current device."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    _check(load().panna_measure_alu_peaks(C.byref(a), C.byref(b), _stream(stream)))
+    return float(a.value), float(b.value)
 
 
 def panna_capture(ctx: int, sysd: "DeviceSystem", theta, prec: int, E_cfg, E_atom, F, virial, stream=None):

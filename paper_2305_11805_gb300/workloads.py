@@ -552,8 +552,49 @@ def bp_variant(wl: Workload, rad_gain: float, ang_gain: float, lambdas=(1.0, -1.
     return dataclasses.replace(wl, name=wl.name + "_bp", desc=desc, archs=archs, theta=theta)
 
 
+# Workloads whose generation takes more than a few seconds are kept in a per-machine cache
+# (a pickle keyed by name, seed and a hash of this file, so any change of the recipe makes
+# a new entry); PANNA_WORKLOAD_CACHE="" switches it off.
+_CACHED = ("ragged4096", "fcc1m")
+
+
+def _cache_path(name: str, seed: int) -> Optional[str]:
+    import hashlib
+    import os
+    import tempfile
+    root = os.environ.get("PANNA_WORKLOAD_CACHE", os.path.join(tempfile.gettempdir(), "panna_workloads"))
+    if not root:
+        return None
+    with open(os.path.abspath(__file__), "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    return os.path.join(root, "%s_seed%d_%s.pkl" % (name, seed, h))
+
+
 def make(name: str, seed: int = 0) -> Workload:
     """Workload by name, including the small variants used by the CPU oracle."""
+    path = _cache_path(name, seed) if name in _CACHED else None
+    if path:
+        import os
+        import pickle
+        try:
+            with open(path, "rb") as f:
+                return pickle.load(f)
+        except (OSError, EOFError, pickle.UnpicklingError):
+            pass
+        wl = _make(name, seed)
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = "%s.%d.tmp" % (path, os.getpid())
+            with open(tmp, "wb") as f:
+                pickle.dump(wl, f, protocol=pickle.HIGHEST_PROTOCOL)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+        return wl
+    return _make(name, seed)
+
+
+def _make(name: str, seed: int) -> Workload:
     table = {
         "diamond64": lambda: diamond64(seed),
         "molecules1024": lambda: molecules(seed, 1024),

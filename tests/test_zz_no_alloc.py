@@ -68,3 +68,44 @@ def test_static_rejects_batches_beyond_its_scratch(torch_cuda):
     st = P.load().panna_descriptors_static(ctypes.byref(h.s), ctypes.byref(big), sysd.s.pos, None)
     assert st == P.PANNA_ERR_INVALID_ARG
     assert b"static" in P.load().panna_last_error()
+
+
+def test_static_reports_neighbour_overflow(torch_cuda):
+    """A dense non-periodic cluster (a 7 x 7 x 7 grid, 1 A apart) with rc = 12 A gives every
+    atom 342 neighbours, more than the 256 slots per atom of the static scratch.  The
+    neighbour kernel writes only the slots below the capacity, so the call is bounded and
+    must report the overflow with the atom and its neighbour count."""
+    torch = torch_cuda
+    g = np.arange(7, dtype=np.float64)
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    n = len(pos)
+    system = W.System(np.array([0, n], np.int64), pos, np.zeros(n, np.int32), np.zeros((1, 9)),
+                      np.zeros((1, 3), np.uint8), 1)
+    desc = W.descriptor_params(1, 12.0, 8, 4, 4)
+    sysd = P.DeviceSystem(system)
+    G = torch.empty((n, desc.D), dtype=torch.float32, device="cuda")
+    with pytest.raises(P.PannaError) as ei:
+        P.panna_descriptors_static(desc, sysd, G)
+    assert ei.value.status == P.PANNA_ERR_NEIGHBOR_OVERFLOW
+    msg = P.load().panna_last_error().decode()
+    assert "342 neighbours" in msg and "atom" in msg, msg
+    # the scratch is usable again afterwards
+    wl = W.make("diamond64")
+    sd = P.DeviceSystem(wl.system)
+    pot = P.Potential(wl.desc, wl.archs)
+    G_ref = pot.descriptors(sd).cpu().numpy().astype(np.float64)
+    G2 = torch.empty((sd.n_atoms, pot.D), dtype=torch.float32, device="cuda")
+    P.panna_descriptors_static(wl.desc, sd, G2)
+    torch.cuda.synchronize()
+    assert H.descriptor_error(G2.cpu().numpy().astype(np.float64), G_ref, wl.desc) <= H.TOL_G
+
+
+def test_static_checks_the_output_buffer(torch_cuda):
+    torch = torch_cuda
+    wl = W.make("diamond64")
+    sysd = P.DeviceSystem(wl.system)
+    with pytest.raises(ValueError):
+        P.panna_descriptors_static(wl.desc, sysd, torch.empty((sysd.n_atoms, wl.desc.D - 1), device="cuda"))
+    with pytest.raises(ValueError):
+        P.panna_descriptors_static(wl.desc, sysd, torch.empty((sysd.n_atoms, wl.desc.D), dtype=torch.float64,
+                                                              device="cuda"))
