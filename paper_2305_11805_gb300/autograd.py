@@ -40,3 +40,47 @@ class PannaEnergyForces(torch.autograd.Function):
 def energy_forces(theta: torch.Tensor, pot: "P.Potential", sysd: "P.DeviceSystem"):
     """Differentiable (E_cfg, F) with respect to theta."""
     return PannaEnergyForces.apply(theta, pot, sysd)
+
+
+class PannaEnergy(torch.autograd.Function):
+    """Per-configuration energies as a differentiable function of the atomic positions (and of
+    the network parameters).  The forward pass is one panna_energy_forces call: descriptors,
+    networks, and the descriptor adjoint, which turns g = dE/dG into the forces
+    F = -dE/dx without materialising dG/dx (Sec. II).  The adjoint is linear in g, so the
+    gradient of any loss L(E) with respect to the positions, dL/dx_i = (dL/dE_c) dE_c/dx_i =
+    -(dL/dE_c) F_i for the configuration c of atom i, is the adjoint's output scaled per
+    configuration; the parameter gradient is the library's reverse pass through the networks.
+    First derivatives only (a loss on the forces goes through PannaEnergyForces instead)."""
+
+    @staticmethod
+    def forward(ctx, pos: torch.Tensor, theta: torch.Tensor, pot: "P.Potential", sysd: "P.DeviceSystem",
+                prec: int):
+        if pos.dtype != torch.float64 or not pos.is_cuda or pos.shape != (sysd.n_atoms, 3):
+            raise TypeError("pos must be a float64 CUDA tensor of shape [n_atoms, 3]")
+        if theta.dtype != torch.float32 or not theta.is_cuda:
+            raise TypeError("theta must be a float32 CUDA tensor")
+        pos_c = pos.detach().contiguous()
+        theta_c = theta.detach().contiguous()
+        s = P.DeviceSystem.from_tensors(sysd.atom_off, pos_c, sysd.species, sysd.cell, sysd.pbc, sysd.ghost)
+        E, _, F, _ = pot.energy_forces(s, theta_c, prec, virial=False, atom_energies=False)
+        cfg = torch.repeat_interleave(torch.arange(sysd.n_cfg, device=pos.device),
+                                      torch.diff(sysd.atom_off))
+        ctx.pot, ctx.sys = pot, s
+        ctx.save_for_backward(theta_c, F, cfg)
+        return E
+
+    @staticmethod
+    def backward(ctx, gE: torch.Tensor):
+        theta, F, cfg = ctx.saved_tensors
+        g = gE.detach().to(torch.float64)
+        gpos = -(g[cfg].unsqueeze(1) * F.double()) if ctx.needs_input_grad[0] else None
+        gth = ctx.pot.param_vjp(ctx.sys, theta, g.contiguous(), None) if ctx.needs_input_grad[1] else None
+        return gpos, gth, None, None, None
+
+
+def energy(pos: torch.Tensor, theta: torch.Tensor, pot: "P.Potential", sysd: "P.DeviceSystem",
+           prec: int = P.PANNA_MLP_FP32):
+    """Differentiable E_cfg with respect to the positions pos [n_atoms, 3] (FP64) and theta:
+    -d(E.sum())/dpos are the forces.  sysd supplies the species, cells, periodic flags and
+    configuration offsets; its own positions are not read."""
+    return PannaEnergy.apply(pos, theta, pot, sysd, prec)

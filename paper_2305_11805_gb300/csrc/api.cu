@@ -64,6 +64,7 @@ struct Arena {
     }
 };
 
+constexpr int kNumVariants = 5;   // descriptor-family kernel variants the tuner measures
 const char* kStages[] = {"neighbors", "descriptor", "mlp", "adjoint", "forces", "jvp", "mlp_grad", "loss"};
 constexpr int kNumStages = 8;
 
@@ -357,10 +358,11 @@ ParamRanges frozen_ranges(const panna_ctx* c)
     return r;
 }
 
-// Kernel variants (0 blocked, 1 flattened) of the descriptor-family kernels for this problem
-// signature: measured once per kernel (each variant launched once to warm up, then timed
-// with CUDA events on the caller's stream), then cached.  Asynchronous calls never measure
-// (they may be under stream capture) and use the cached or default choice.
+// Kernel variants of the descriptor-family kernels for this problem signature (0 blocked,
+// 1 flattened, 2 / 3 / 4 compensated with 32 / 16 / 8 lanes per unit): measured once per kernel
+// (each variant launched once to warm up, then timed with CUDA events on the caller's stream),
+// then cached.  Asynchronous calls never measure (they may be under stream capture) and use
+// the cached or default choice.
 enum { KV_DESC = 0, KV_ADJ = 1, KV_JVP = 2 };
 
 template <class Launch>
@@ -373,18 +375,19 @@ int tuned_variant(panna_ctx* c, const panna_system* sys, int prec, int kind, cud
         if (q.N == sys->n_atoms && q.C == sys->n_cfg && q.cap == c->cap && q.prec == prec) t = &q;
     }
     if (t && t->variant[kind] >= 0) return t->variant[kind];
-    const int fallback = c->d.S > 1 ? 1 : 0;
+    const int fallback = sys->n_atoms < kSplitAtoms ? 0 : 2;
     if (!c->autotune || c->async || sys->n_atoms == 0) return fallback;
-    float ms[2] = {0.f, 0.f};
-    for (int v = 0; v < 2; ++v) launch(v);   // first launches load and configure the kernels
-    for (int v = 0; v < 2; ++v) {
+    float ms[kNumVariants] = {};
+    for (int v = 0; v < kNumVariants; ++v) launch(v);   // first launches load and configure the kernels
+    int best = 0;
+    for (int v = 0; v < kNumVariants; ++v) {
         cudaEventRecord(c->tev[0], s);
         launch(v);
         cudaEventRecord(c->tev[1], s);
         cudaEventSynchronize(c->tev[1]);
         cudaEventElapsedTime(&ms[v], c->tev[0], c->tev[1]);
+        if (ms[v] < ms[best]) best = v;
     }
-    const int best = ms[1] < ms[0] ? 1 : 0;
     if (!t) {
         t = &c->tuned[c->n_tuned < 16 ? c->n_tuned++ : 15];
         *t = panna_ctx::Tuned{sys->n_atoms, sys->n_cfg, c->cap, prec, {-1, -1, -1}};
@@ -405,6 +408,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     c->n_marked = 0;
     CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
     const StoreView* sv = rq.store;
+    bool g16_ready = false;   // BF16 networks: the descriptor kernel wrote their operand rows
     if (sv) {
         // stored descriptors: rows, maps and configuration indices come from the store
         L.w.row_of_atom = sv->row_of_atom;
@@ -421,7 +425,9 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         else CU(build_neighbors(L.w, c->d, s, &nl));
         if (rq.G_out) {
             stage_mark(c, 1, s);
-            CU(launch_descriptor(L.w, c->d, rq.G_out, nullptr, c->ang_mode != 2, s, &nl));
+            const int fv = c->force_variant[KV_DESC];
+            CU(launch_descriptor(L.w, c->d, rq.G_out, nullptr, c->ang_mode != 2, s, &nl,
+                                 fv >= 0 ? fv : (sys->n_atoms < kSplitAtoms ? 0 : 2)));
             if (c->profiling) cudaEventRecord(c->ev[kNumStages], s);
             return PANNA_OK;
         }
@@ -432,7 +438,17 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         const int v = tuned_variant(c, sys, rq.prec, KV_DESC, s, [&](int vv) {
             launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &dummy, vv);
         });
-        CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl, v));
+        const bool tcp = rq.prec == PANNA_MLP_BF16 || rq.prec == PANNA_MLP_BF16_FAST;
+        __nv_bfloat16 *gh = nullptr, *gl = nullptr;
+        if (tcp) tc_g16(c->plan, N, rq.prec == PANNA_MLP_BF16, L.tc_ws, &gh, &gl);
+        cudaError_t eb = gh ? launch_descriptor_bf16(L.w, c->d, gh, gl, L.w.row_of_atom, v, s, &nl)
+                            : cudaErrorNotSupported;
+        if (eb == cudaErrorNotSupported) {
+            CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl, v));
+        } else {
+            CU(eb);
+            g16_ready = true;
+        }
     }
     stage_mark(c, 2, s);
     float* F = rq.F ? rq.F : L.F_int;
@@ -444,7 +460,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     if (tc) {
         // BF16 operands on the tensor cores: energies and dE/dG together
         CU(mlp_bf16_energy_grad(c->plan, L.mb, rq.theta, N, L.tc_ws, rq.prec == PANNA_MLP_BF16, L.E_rows, L.g,
-                                L.w.status, s, &nl));
+                                L.w.status, s, &nl, g16_ready));
     } else if (tf) {
         // FP32 networks: first-layer products on the tensor cores (TF32 parts), the rest on CUDA cores
         CU(tf32_prepare(c->plan, L.mb, rq.theta, N, L.tf_ws, tfm, s, &nl));
@@ -723,7 +739,7 @@ panna_status panna_set_tuning(panna_ctx* c, const char* knob, int32_t value)
     }
     const char* kinds[3] = {"descriptor", "adjoint", "jvp"};
     for (int k = 0; k < 3; ++k)
-        if (strcmp(knob, kinds[k]) == 0 && value >= -1 && value <= 1) {
+        if (strcmp(knob, kinds[k]) == 0 && value >= -1 && value < kNumVariants) {
             c->force_variant[k] = value;
             return PANNA_OK;
         }

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libpanna_gb300.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,6 +44,9 @@ struct DescDev {
     float half_cos_lo[kMaxTheta];  // remainders: exact value - float value
     float half_sin_lo[kMaxTheta];
     float eps_theta_lo;
+    float cos_half_t[kMaxTheta];   // cos(theta_m / 2), sin(theta_m / 2) (half-angle form)
+    float sin_half_t[kMaxTheta];
+    float zpoly[5];                // zeta log2(e) log(y) = w (c0 + c1 w^2 + ... + c4 w^8), w = t / (2 - t)
     // standard BP angular term (ang_kind 1): sector m = (lambda_m, zeta_m), shell n = eta_n
     int32_t ang_kind;              // 0 = modified (mBP), 1 = standard BP
     float bp_lambda[kMaxTheta], bp_zeta[kMaxTheta], bp_pref[kMaxTheta];   // pref = 2^(1 - zeta)
@@ -137,6 +141,11 @@ cudaError_t launch_descriptor(const Work& w, const DescDev& d, float* G_rows, co
                               cudaStream_t s, int* launches, int variant = 0);
 cudaError_t launch_adjoint(const Work& w, const DescDev& d, const float* g_rows, float* F, float* vir_atom, bool acc,
                            int variant, cudaStream_t s, int* launches);
+// descriptor rows written straight into the BF16 hi (+ lo) operands of the tensor-core networks
+// (compensated variants 2..4 of the modified term, batches that need no atom splits);
+// cudaErrorNotSupported otherwise (then write FP32 rows and convert)
+cudaError_t launch_descriptor_bf16(const Work& w, const DescDev& d, __nv_bfloat16* Gh, __nv_bfloat16* Gl,
+                                   const int32_t* row_map, int variant, cudaStream_t s, int* launches);
 cudaError_t launch_jvp(const Work& w, const DescDev& d, const float* u, float* wdot_rows, bool acc, cudaStream_t s,
                        int* launches, int variant = 0);
 

@@ -54,9 +54,14 @@ cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
                            cudaStream_t s, int* launches, float** ab1 = nullptr, bool seeded = false);
 // BF16 tensor-core networks (mlp_tc.cu): energies and input gradients; ws from tc_workspace_bytes
 size_t tc_workspace_bytes(const MlpPlan& p, int64_t N, bool split);
+// g16_ready: the descriptor kernel already wrote the BF16 operand rows (tc_g16), else the FP32
+// rows b.G are converted first
 cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, void* ws,
                                  bool split, float* E_rows, float* g, DevStatus* status, cudaStream_t s,
-                                 int* launches);
+                                 int* launches, bool g16_ready = false);
+// the BF16 descriptor operand rows (hi, lo; lo null without split) inside the workspace ws, or
+// null when the descriptor width is not a multiple of 8
+void tc_g16(const MlpPlan& p, int64_t N, bool split, void* ws, __nv_bfloat16** hi, __nv_bfloat16** lo);
 struct WgradTc;
 // Parts of the weight-gradient pass: both (default); the forward tangent along wdot only (the
 // output tangents land in b.Ad[L]); or the reverse pass only, with the output seeds already in

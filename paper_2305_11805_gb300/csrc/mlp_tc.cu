@@ -855,6 +855,233 @@ cudaError_t launch_tc_grid(const TcMaps& m, const TcArgs& ta, dim3 grid, cudaStr
     return cudaGetLastError();
 }
 
+// Persistent form of the row-tiled GEMM for the BF16 networks' layers (TC_FWD, TC_BWD_MID,
+// TC_BWD_OUT).  One CTA per SM walks the work items (128-row tile of one species x N tile)
+// with a stride of the grid size.  The TMA warp runs ahead through the stage ring across item
+// boundaries; the MMA warp alternates between two TMEM accumulators, so the epilogue warps
+// drain item j (tcgen05.ld, bias / activation, stores straight from registers: each thread
+// writes whole 32-byte sectors of its own row) while the MMAs of item j + 1 run.  Barriers:
+// full / empty per stage (TMA <-> MMA), acc_full / acc_empty per accumulator (MMA <->
+// epilogue, the latter counting one arrival per epilogue warp).  Every wait is bounded.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct ItemPos {
+    int s, row0, rend, n0;
+    bool valid;
+};
+
+__device__ __forceinline__ ItemPos tc_item(const TcArgs& a, int item, int n_nt)
+{
+    ItemPos p;
+    const int tile = item / n_nt, nt = item - tile * n_nt;
+    int s = 0;
+    while (tile >= a.tile_start[s + 1]) ++s;
+    p.s = s;
+    p.n0 = nt * a.BN;
+    p.row0 = a.seg_off[s] + (tile - a.tile_start[s]) * kTcBM;
+    p.rend = a.seg_off[s + 1];
+    p.valid = p.n0 < a.N[s];
+    return p;
+}
+
+template <int EPI, int PARTS>
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_tc_gemm_p(const __grid_constant__ TcMaps tm, TcArgs a, int n_nt)
+{
+    using Cfg = TcCfg<PARTS>;
+    constexpr int kStages = Cfg::kStages;
+    constexpr int BKE = kTcBK;                           // BF16 elements per 128-byte K chunk
+    constexpr int MMAK = 16;                             // K per instruction
+    constexpr uint32_t kAcc = Cfg::kMaxBN;               // TMEM columns per accumulator
+    extern __shared__ unsigned char smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kStages * Cfg::kStageA;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * Cfg::kStageB);
+    uint64_t* empty = full + kStages;
+    uint64_t* accf = empty + kStages;                    // [2]
+    uint64_t* acce = accf + 2;                           // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_items = a.tile_start[a.S] * n_nt;
+    const int nk = (a.K + BKE - 1) / BKE;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) { mbar_init(full + i, 1); mbar_init(empty + i, 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(accf + i, 1); mbar_init(acce + i, kTcEpiWarps); }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, 2 * kAcc);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t bytes = Cfg::kParts * (kTileA + (uint32_t)a.BN * 128u);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int g = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                const ItemPos ip = tc_item(a, item, n_nt);
+                if (!ip.valid) continue;
+                for (int kc = 0; kc < nk; ++kc, ++g) {
+                    const int st = g % kStages;
+                    const uint32_t ph = (uint32_t)(g / kStages) & 1u;
+                    if (!mbar_wait(empty + st, ph ^ 1u, abort_flag)) { *abort_flag = 1; ok = false; break; }
+                    mbar_expect_tx(full + st, bytes);
+                    uint8_t* a_st = sA + st * Cfg::kStageA;
+                    uint8_t* b_st = sB + st * Cfg::kStageB;
+#pragma unroll
+                    for (int q = 0; q < PARTS; ++q) {
+                        tma_load_2d(a_st + q * kTileA, &tm.a[q], kc * BKE, ip.row0, full + st);
+                        tma_load_2d(b_st + q * Cfg::kTileB, &tm.b[q], kc * BKE, ip.s * a.n_pad + ip.n0, full + st);
+                    }
+                }
+            }
+            // never leave with copies in flight
+            for (int k = g > kStages ? g - kStages : 0; k < g; ++k)
+                mbar_wait(full + k % kStages, (uint32_t)(k / kStages) & 1u, nullptr);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_mma(false, kTcBM, (uint32_t)a.BN);
+            int g = 0, j = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                const ItemPos ip = tc_item(a, item, n_nt);
+                if (!ip.valid) continue;
+                const int b = j & 1;
+                if (!mbar_wait(acce + b, ((uint32_t)(j >> 1) & 1u) ^ 1u, abort_flag)) { *abort_flag = 1; break; }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)b * kAcc;
+                for (int kc = 0; kc < nk; ++kc, ++g) {
+                    const int st = g % kStages;
+                    const uint32_t ph = (uint32_t)(g / kStages) & 1u;
+                    if (!mbar_wait(full + st, ph, abort_flag)) { *abort_flag = 1; ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + st * Cfg::kStageA), b0 = smem_u32(sB + st * Cfg::kStageB);
+#pragma unroll
+                    for (int kk = 0; kk < BKE / MMAK; ++kk) {
+                        const uint64_t a1 = sw128_desc(a0 + kk * 32), b1 = sw128_desc(b0 + kk * 32);
+                        tc_mma<false>(d, a1, b1, idesc, (kc | kk) ? 1u : 0u);
+                        if (PARTS >= 2) {
+                            const uint64_t a2 = sw128_desc(a0 + kTileA + kk * 32);
+                            const uint64_t b2 = sw128_desc(b0 + Cfg::kTileB + kk * 32);
+                            tc_mma<false>(d, a1, b2, idesc, 1u);
+                            tc_mma<false>(d, a2, b1, idesc, 1u);
+                        }
+                    }
+                    tc_commit(empty + st);
+                }
+                tc_commit(accf + b);   // arrives once the item's MMAs have completed
+                ++j;
+            }
+            // no TMEM release under running MMAs: the epilogue waited for every committed item;
+            // after an abort wait (bounded) for whatever was issued last
+            if (!ok || *abort_flag) {
+                tc_commit(accf + (j & 1));
+                mbar_wait(accf + (j & 1), ((uint32_t)(j >> 1) & 1u), nullptr);
+            }
+        }
+    } else {
+        const int ew = warp - 2;
+        const int q = warp & 3;                    // TMEM lane quarter of this warp
+        const int half = ew >> 2;
+        int j = 0;
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+            const ItemPos ip = tc_item(a, item, n_nt);
+            if (!ip.valid) continue;
+            const int b = j & 1;
+            if (!mbar_wait(accf + b, (uint32_t)(j >> 1) & 1u, abort_flag)) { *abort_flag = 1; break; }
+            tc_fence_after();
+            const int r = ip.row0 + q * 32 + lane;
+            const bool row_ok = r < ip.rend;
+            const int s = ip.s, Ns = a.N[s];
+            for (int c0 = half * 16; c0 < a.BN; c0 += 32) {
+                float v[16];
+                tc_ld16(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                const int n = ip.n0 + c0;
+                if (!row_ok || n >= Ns) continue;
+                const bool whole = n + 16 <= Ns;
+                float o1[16], o2[16];
+                if (EPI == TC_FWD) {
+                    const float* bias = a.bias + s * a.n_pad + n;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        o1[k] = v[k] + bias[k];
+                        o2[k] = act_f(a.act[s], o1[k]);
+                    }
+                } else if (EPI == TC_BWD_MID) {
+                    const float* z = a.Zin + (size_t)r * a.ldZ + n;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) o2[k] = (whole || n + k < Ns) ? v[k] * act_d1(a.act[s], z[k]) : 0.f;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) o1[k] = v[k];
+                }
+                if (EPI == TC_FWD || EPI == TC_BWD_OUT) {
+                    float* o = a.outF + (size_t)r * a.ldF + n;
+                    if (whole && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+#pragma unroll
+                        for (int k = 0; k < 16; k += 4)
+                            *reinterpret_cast<float4*>(o + k) = make_float4(o1[k], o1[k + 1], o1[k + 2], o1[k + 3]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k)
+                            if (n + k < Ns) o[k] = o1[k];
+                    }
+                }
+                if (EPI == TC_FWD || EPI == TC_BWD_MID) {
+                    __nv_bfloat16* oh = a.outH + (size_t)r * a.ldH + n;
+                    __nv_bfloat16* ol = PARTS >= 2 ? a.outL + (size_t)r * a.ldH + n : nullptr;
+                    if (whole && (reinterpret_cast<uintptr_t>(oh) & 15) == 0) {
+                        uint32_t hw[8], lw[8];
+#pragma unroll
+                        for (int k = 0; k < 16; k += 2) {
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(o2[k]), h1 = __float2bfloat16_rn(o2[k + 1]);
+                            const __nv_bfloat16 l0 = __float2bfloat16_rn(o2[k] - __bfloat162float(h0));
+                            const __nv_bfloat16 l1 = __float2bfloat16_rn(o2[k + 1] - __bfloat162float(h1));
+                            hw[k / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                            lw[k / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                        }
+                        uint4* dh = reinterpret_cast<uint4*>(oh);
+                        dh[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        dh[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+                        if (PARTS >= 2) {
+                            uint4* dl = reinterpret_cast<uint4*>(ol);
+                            dl[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                            dl[1] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k)
+                            if (n + k < Ns)
+                                store_split(a.outH, PARTS >= 2 ? a.outL : nullptr, (size_t)r * a.ldH + n + k, o2[k]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce + b);
+            ++j;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) set_status(a.status, PANNA_ERR_TIMEOUT, blockIdx.x);
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * kAcc);
+    }
+}
+
 // row-tiled launch: one CTA per (species, 128-row tile) and N tile
 template <int EPI, int PARTS, bool TF = false>
 cudaError_t launch_tc(const TcMaps& m, const TcArgs& ta, int64_t N, int nmax, cudaStream_t s)
@@ -863,10 +1090,31 @@ cudaError_t launch_tc(const TcMaps& m, const TcArgs& ta, int64_t N, int nmax, cu
     return launch_tc_grid<EPI, PARTS, TF>(m, ta, grid, s);
 }
 
+// persistent launch: one CTA per SM (at most one per work item)
+template <int EPI, int PARTS>
+cudaError_t launch_tc_p(const TcMaps& m, const TcArgs& ta, int64_t N, int nmax, cudaStream_t s)
+{
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    const int n_nt = (nmax + ta.BN - 1) / ta.BN;
+    const int64_t items = ((N + kTcBM - 1) / kTcBM + ta.S) * n_nt;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, n_sm);
+    const int smem = (int)TcCfg<PARTS>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_p<EPI, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm_p<EPI, PARTS><<<grid, kTcThreads, smem, s>>>(m, ta, n_nt);
+    return cudaGetLastError();
+}
+
 template <int EPI>
 cudaError_t launch_tc_any(bool split, const TcMaps& m, const TcArgs& ta, int64_t N, int nmax, cudaStream_t s)
 {
-    return split ? launch_tc<EPI, 2>(m, ta, N, nmax, s) : launch_tc<EPI, 1>(m, ta, N, nmax, s);
+    return split ? launch_tc_p<EPI, 2>(m, ta, N, nmax, s) : launch_tc_p<EPI, 1>(m, ta, N, nmax, s);
 }
 
 // Buffers of the BF16 networks, carved from one workspace block (sizing when base == nullptr).
@@ -939,9 +1187,17 @@ size_t tc_workspace_bytes(const MlpPlan& p, int64_t N, bool split)
 // GEMMs (FP32 accumulation).  split: every BF16 operand is carried as a hi + lo pair and each
 // product takes three MMAs (hi*hi + hi*lo + lo*hi), about 16 significant bits per operand.
 // G rows in FP32 are converted first.  Needs at least one hidden layer.
+void tc_g16(const MlpPlan& p, int64_t N, bool split, void* ws, __nv_bfloat16** hi, __nv_bfloat16** lo)
+{
+    TcBufs t;
+    tc_carve(p, N, split, static_cast<char*>(ws), t);
+    *hi = t.ldh[0] == p.ld[0] ? t.G16[0] : nullptr;
+    *lo = t.ldh[0] == p.ld[0] ? t.G16[1] : nullptr;
+}
+
 cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const float* theta, int64_t N, void* ws,
                                  bool split, float* E_rows, float* g, DevStatus* status, cudaStream_t s,
-                                 int* launches)
+                                 int* launches, bool g16_ready)
 {
     if (p.L < 2) return cudaErrorNotSupported;
     cudaError_t e = get_encoder();
@@ -970,8 +1226,10 @@ cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const fl
             if (e == cudaSuccess) e = cudaMemsetAsync(t.Zb16[l][q], 0, (size_t)N * t.ldh[l] * 2, s);
             if (e != cudaSuccess) return e;
         }
-    k_to_bf16<<<(unsigned)((N * t.ldh[0] + 255) / 256), 256, 0, s>>>(N * t.ldh[0], b.G, t.G16[0], t.G16[1]);
-    ++*launches;
+    if (!g16_ready) {
+        k_to_bf16<<<(unsigned)((N * t.ldh[0] + 255) / 256), 256, 0, s>>>(N * t.ldh[0], b.G, t.G16[0], t.G16[1]);
+        ++*launches;
+    }
 
     TcArgs base{};
     base.S = p.S;

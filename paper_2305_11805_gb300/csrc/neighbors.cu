@@ -355,21 +355,29 @@ constexpr int kNbWarps = 8;
 
 // Rare paths with FP64 arithmetic, kept out of line: GB300 runs FP64 at 1/64 of the FP32
 // rate, and the hot loop must not carry (even predicated-off) FP64 instructions.
-__device__ __noinline__ void shift_hilo(const CfgGeom& g, int t0, int t1, int t2, float* shh, float* shl)
+struct Shift6 {
+    float h0, h1, h2, l0, l1, l2;   // image shift as hi + lo floats
+};
+
+__device__ __noinline__ Shift6 shift_hilo(const CfgGeom& g, int t0, int t1, int t2)
 {
+    Shift6 r;
+    float h[3], l[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
         double Sv = t0 * g.cell[d] + t1 * g.cell[3 + d] + t2 * g.cell[6 + d];
-        shh[d] = (float)Sv;
-        shl[d] = (float)(Sv - (double)shh[d]);
+        h[d] = (float)Sv;
+        l[d] = (float)(Sv - (double)h[d]);
     }
+    r.h0 = h[0]; r.h1 = h[1]; r.h2 = h[2]; r.l0 = l[0]; r.l1 = l[1]; r.l2 = l[2];
+    return r;
 }
 
-__device__ __noinline__ bool retest_fp64(float4 xjh, float4 xjl, const float* shh, const float* shl, float4 xih,
-                                         float4 xil, double rc2d)
+__device__ __noinline__ bool retest_fp64(float4 xjh, float4 xjl, Shift6 sh, float4 xih, float4 xil, double rc2d)
 {
-    double rx = ((double)xjh.x + (double)xjl.x) + ((double)shh[0] + (double)shl[0]) - ((double)xih.x + (double)xil.x);
-    double ry = ((double)xjh.y + (double)xjl.y) + ((double)shh[1] + (double)shl[1]) - ((double)xih.y + (double)xil.y);
-    double rz = ((double)xjh.z + (double)xjl.z) + ((double)shh[2] + (double)shl[2]) - ((double)xih.z + (double)xil.z);
+    double rx = ((double)xjh.x + (double)xjl.x) + ((double)sh.h0 + (double)sh.l0) - ((double)xih.x + (double)xil.x);
+    double ry = ((double)xjh.y + (double)xjl.y) + ((double)sh.h1 + (double)sh.l1) - ((double)xih.y + (double)xil.y);
+    double rz = ((double)xjh.z + (double)xjl.z) + ((double)sh.h2 + (double)sh.l2) - ((double)xih.z + (double)xil.z);
     return (rx * rx + ry * ry + rz * rz) < rc2d;
 }
 
@@ -403,66 +411,107 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
     const double rc2d = rc_d * rc_d;
     const unsigned lt = (1u << lane) - 1u;
     int count = 0;
-    for (int d0 = -g.K[0]; d0 <= g.K[0]; ++d0) {
-        int c0 = ci0 + d0, t0 = 0;
-        if (g.per[0]) { t0 = (c0 >= 0 ? c0 / n0 : -((-c0 + n0 - 1) / n0)); c0 -= t0 * n0; }
-        else if (c0 < 0 || c0 >= n0) continue;
-        for (int d1 = -g.K[1]; d1 <= g.K[1]; ++d1) {
-            int c1 = ci1 + d1, t1 = 0;
+    // The window of (2K+1)^3 cells around the atom's cell, 32 cells at a time (one per lane):
+    // each lane resolves its cell (periodic wrap, image shift, atom range), a warp scan gives
+    // every cell's offset in the concatenated candidate list, and the lanes then take the
+    // candidates 32 at a time, each finding its cell by a binary search over the lanes'
+    // offsets.  Cells are visited in the same order as a nested (d0, d1, d2) loop, atoms in
+    // cell order, so the neighbour order is deterministic.
+    const int W1 = 2 * g.K[1] + 1, W2 = 2 * g.K[2] + 1;
+    const int nwin = (2 * g.K[0] + 1) * W1 * W2;
+    for (int cb = 0; cb < nwin; cb += 32) {
+        const int wc = cb + lane;
+        int cnt = 0, tcode = 0;
+        int64_t beg = 0;
+        Shift6 sh{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (wc < nwin) {
+            const int d0 = wc / (W1 * W2) - g.K[0], d1 = (wc / W2) % W1 - g.K[1], d2 = wc % W2 - g.K[2];
+            int c0 = ci0 + d0, c1 = ci1 + d1, c2 = ci2 + d2, t0 = 0, t1 = 0, t2 = 0;
+            bool ok = true;
+            if (g.per[0]) { t0 = (c0 >= 0 ? c0 / n0 : -((-c0 + n0 - 1) / n0)); c0 -= t0 * n0; }
+            else ok = ok && c0 >= 0 && c0 < n0;
             if (g.per[1]) { t1 = (c1 >= 0 ? c1 / n1 : -((-c1 + n1 - 1) / n1)); c1 -= t1 * n1; }
-            else if (c1 < 0 || c1 >= n1) continue;
-            for (int d2 = -g.K[2]; d2 <= g.K[2]; ++d2) {
-                int c2 = ci2 + d2, t2 = 0;
-                if (g.per[2]) { t2 = (c2 >= 0 ? c2 / n2 : -((-c2 + n2 - 1) / n2)); c2 -= t2 * n2; }
-                else if (c2 < 0 || c2 >= n2) continue;
-                float shh[3], shl[3];
-                if (t0 >= -1 && t0 <= 1 && t1 >= -1 && t1 <= 1 && t2 >= -1 && t2 <= 1) {
-                    int k = (t0 + 1) * 9 + (t1 + 1) * 3 + (t2 + 1);
-                    for (int d = 0; d < 3; ++d) { shh[d] = g.sh_hi[k][d]; shl[d] = g.sh_lo[k][d]; }
-                } else {
-                    shift_hilo(g, t0, t1, t2, shh, shl);
-                }
-                const bool self_image = (t0 == 0 && t1 == 0 && t2 == 0);
+            else ok = ok && c1 >= 0 && c1 < n1;
+            if (g.per[2]) { t2 = (c2 >= 0 ? c2 / n2 : -((-c2 + n2 - 1) / n2)); c2 -= t2 * n2; }
+            else ok = ok && c2 >= 0 && c2 < n2;
+            if (ok) {
                 const int64_t gc = g.cell_base + (c0 * n1 + c1) * n2 + c2;
-                const int64_t b = cell_start[gc], e = cell_start[gc + 1];
-                for (int64_t base = b; base < e; base += 32) {
-                    const int64_t q = base + lane;
-                    bool in = false;
-                    float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-                    int j = -1, spj = 0;
-                    if (q < e) {
-                        j = cell_atoms[q];
-                        const float4 xjh = pos_hi[j];
-                        spj = __float_as_int(xjh.w);
-                        float fx = (xjh.x + shh[0]) - xih.x;
-                        float fy = (xjh.y + shh[1]) - xih.y;
-                        float fz = (xjh.z + shh[2]) - xih.z;
-                        float f2 = fx * fx + fy * fy + fz * fz;
-                        if (f2 < band2 && !(self_image && j == (int)i)) {
-                            const float4 xjl = pos_lo[j];
-                            dx = dd_rel(xjh.x, xjl.x, shh[0], shl[0], xih.x, xil.x);
-                            dy = dd_rel(xjh.y, xjl.y, shh[1], shl[1], xih.y, xil.y);
-                            dz = dd_rel(xjh.z, xjl.z, shh[2], shl[2], xih.z, xil.z);
-                            r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
-                            if (fabsf(r2 - rc2) <= 2e-6f * rc2) {
-                                in = retest_fp64(xjh, xjl, shh, shl, xih, xil, rc2d);   // FP64 near the cutoff
-                            } else {
-                                in = r2 < rc2;
-                            }
-                            if (in && r2 == 0.f) { set_status(st, PANNA_ERR_BAD_INPUT, (int)i); in = false; }
-                        }
-                    }
-                    const unsigned mask = __ballot_sync(0xffffffffu, in);
-                    if (in) {
-                        int pos = count + __popc(mask & lt);
-                        if (pos < cap) {
-                            svec[pos] = make_float4(dx, dy, dz, sqrtf(r2));
-                            sidx[pos] = make_int2(j, pack_meta(t0, t1, t2, spj));
-                        }
-                    }
-                    count += __popc(mask);
+                beg = cell_start[gc];
+                cnt = (int)(cell_start[gc + 1] - beg);
+                tcode = pack_meta(t0, t1, t2, 0);
+                if (t0 >= -1 && t0 <= 1 && t1 >= -1 && t1 <= 1 && t2 >= -1 && t2 <= 1) {
+                    const int k = (t0 + 1) * 9 + (t1 + 1) * 3 + (t2 + 1);
+                    sh = Shift6{g.sh_hi[k][0], g.sh_hi[k][1], g.sh_hi[k][2], g.sh_lo[k][0], g.sh_lo[k][1],
+                                g.sh_lo[k][2]};
+                } else {
+                    sh = shift_hilo(g, t0, t1, t2);
                 }
             }
+        }
+        // exclusive offsets of the cells' candidates
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int pre = incl - cnt;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int base = 0; base < total; base += 32) {
+            const int q = base + lane;
+            // the cell slot of candidate q: the last lane whose offset is <= q (empty cells
+            // share an offset with the next one and lose the search)
+            int sl = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int pr = __shfl_sync(0xffffffffu, pre, sl + step);
+                if (pr <= q) sl += step;
+            }
+            const int pre_s = __shfl_sync(0xffffffffu, pre, sl);
+            const int64_t beg_s = __shfl_sync(0xffffffffu, beg, sl);
+            const int tc = __shfl_sync(0xffffffffu, tcode, sl);
+            Shift6 cs;
+            cs.h0 = __shfl_sync(0xffffffffu, sh.h0, sl);
+            cs.h1 = __shfl_sync(0xffffffffu, sh.h1, sl);
+            cs.h2 = __shfl_sync(0xffffffffu, sh.h2, sl);
+            cs.l0 = __shfl_sync(0xffffffffu, sh.l0, sl);
+            cs.l1 = __shfl_sync(0xffffffffu, sh.l1, sl);
+            cs.l2 = __shfl_sync(0xffffffffu, sh.l2, sl);
+            bool in = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            int j = -1, spj = 0;
+            if (q < total) {
+                j = cell_atoms[beg_s + (q - pre_s)];
+                const float4 xjh = pos_hi[j];
+                spj = __float_as_int(xjh.w);
+                const float fx = (xjh.x + cs.h0) - xih.x;
+                const float fy = (xjh.y + cs.h1) - xih.y;
+                const float fz = (xjh.z + cs.h2) - xih.z;
+                const float f2 = fx * fx + fy * fy + fz * fz;
+                const bool self_image = (tc & 0xffffff) == pack_meta(0, 0, 0, 0);
+                if (f2 < band2 && !(self_image && j == (int)i)) {
+                    const float4 xjl = pos_lo[j];
+                    dx = dd_rel(xjh.x, xjl.x, cs.h0, cs.l0, xih.x, xil.x);
+                    dy = dd_rel(xjh.y, xjl.y, cs.h1, cs.l1, xih.y, xil.y);
+                    dz = dd_rel(xjh.z, xjl.z, cs.h2, cs.l2, xih.z, xil.z);
+                    r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+                    if (fabsf(r2 - rc2) <= 2e-6f * rc2) {
+                        in = retest_fp64(xjh, xjl, cs, xih, xil, rc2d);   // FP64 near the cutoff
+                    } else {
+                        in = r2 < rc2;
+                    }
+                    if (in && r2 == 0.f) { set_status(st, PANNA_ERR_BAD_INPUT, (int)i); in = false; }
+                }
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, in);
+            if (in) {
+                const int pos = count + __popc(mask & lt);
+                if (pos < cap) {
+                    svec[pos] = make_float4(dx, dy, dz, sqrtf(r2));
+                    sidx[pos] = make_int2(j, tc | (spj << 24));
+                }
+            }
+            count += __popc(mask);
         }
     }
     if (count > cap && lane == 0) {
@@ -543,22 +592,22 @@ k_refresh(int64_t N, double rc_d, float rc, const CfgGeom* __restrict__ geom, co
         if (k < nc) {
             e = cand_idx[cin + k];
             const int t0 = meta_t(e.y, 0), t1 = meta_t(e.y, 1), t2 = meta_t(e.y, 2);
-            float shh[3], shl[3];
+            Shift6 cs;
             if (t0 >= -1 && t0 <= 1 && t1 >= -1 && t1 <= 1 && t2 >= -1 && t2 <= 1) {
                 const int q = (t0 + 1) * 9 + (t1 + 1) * 3 + (t2 + 1);
-                for (int d = 0; d < 3; ++d) { shh[d] = g.sh_hi[q][d]; shl[d] = g.sh_lo[q][d]; }
+                cs = Shift6{g.sh_hi[q][0], g.sh_hi[q][1], g.sh_hi[q][2], g.sh_lo[q][0], g.sh_lo[q][1], g.sh_lo[q][2]};
             } else {
-                shift_hilo(g, t0, t1, t2, shh, shl);
+                cs = shift_hilo(g, t0, t1, t2);
             }
             const float4 xjh = pos_hi[e.x];
-            const float fx = (xjh.x + shh[0]) - xih.x, fy = (xjh.y + shh[1]) - xih.y, fz = (xjh.z + shh[2]) - xih.z;
+            const float fx = (xjh.x + cs.h0) - xih.x, fy = (xjh.y + cs.h1) - xih.y, fz = (xjh.z + cs.h2) - xih.z;
             if (fx * fx + fy * fy + fz * fz < band2) {
                 const float4 xjl = pos_lo[e.x];
-                dx = dd_rel(xjh.x, xjl.x, shh[0], shl[0], xih.x, xil.x);
-                dy = dd_rel(xjh.y, xjl.y, shh[1], shl[1], xih.y, xil.y);
-                dz = dd_rel(xjh.z, xjl.z, shh[2], shl[2], xih.z, xil.z);
+                dx = dd_rel(xjh.x, xjl.x, cs.h0, cs.l0, xih.x, xil.x);
+                dy = dd_rel(xjh.y, xjl.y, cs.h1, cs.l1, xih.y, xil.y);
+                dz = dd_rel(xjh.z, xjl.z, cs.h2, cs.l2, xih.z, xil.z);
                 r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
-                if (fabsf(r2 - rc2) <= 2e-6f * rc2) in = retest_fp64(xjh, xjl, shh, shl, xih, xil, rc2d);
+                if (fabsf(r2 - rc2) <= 2e-6f * rc2) in = retest_fp64(xjh, xjl, cs, xih, xil, rc2d);
                 else in = r2 < rc2;
                 if (in && r2 == 0.f) { set_status(st, PANNA_ERR_BAD_INPUT, (int)i); in = false; }
             }

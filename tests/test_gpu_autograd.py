@@ -60,3 +60,47 @@ def test_autograd_energy_only_and_force_only(torch_cuda):
     E, F = energy_forces(theta, pot, sysd)
     (E.sum() + (F ** 2).sum()).backward()
     assert torch.allclose(theta.grad, gE + gF, rtol=1e-5, atol=1e-6 * float(theta.grad.abs().max()))
+
+
+@pytest.mark.parametrize("name", ["molecules16", "ragged8", "diamond64"])
+def test_autograd_positions_give_forces(torch_cuda, name):
+    """-dE/dx through the autograd Function (backward = the descriptor adjoint) against the
+    FP64 oracle's forces, a per-configuration upstream gradient, and central differences of
+    the GPU energies themselves."""
+    torch = torch_cuda
+    from paper_2305_11805_gb300.autograd import energy
+    wl = W.make(name)
+    pot = P.Potential(wl.desc, wl.archs)
+    sysd = P.DeviceSystem(wl.system)
+    th32 = wl.theta.astype(np.float32)
+    theta = torch.tensor(th32, device="cuda", requires_grad=True)
+    pos = sysd.pos.clone().requires_grad_(True)
+    E = energy(pos, theta, pot, sysd)
+    E.sum().backward()
+    ref = O.batch(wl.system, wl.desc, wl.archs, th32.astype(np.float64))
+    ferr, rms = H.force_error(-pos.grad.cpu().numpy(), ref["F"])
+    assert ferr <= H.TOL_F_FP32, ferr
+    # per-configuration weights: dL/dx_i = w_c dE_c/dx_i
+    w = torch.linspace(0.5, 2.0, sysd.n_cfg, dtype=torch.float64, device="cuda")
+    pos.grad = None
+    theta.grad = None
+    (w * energy(pos, theta, pot, sysd)).sum().backward()
+    cfg = np.repeat(np.arange(sysd.n_cfg), np.diff(wl.system.atom_off))
+    want = -ref["F"] * w.cpu().numpy()[cfg][:, None]
+    assert H.force_error(pos.grad.cpu().numpy(), want)[0] <= H.TOL_F_FP32
+    # the parameter gradient of sum_c w_c E_c equals the VJP with dE = w
+    g2 = pot.param_vjp(sysd, theta.detach(), w, None)
+    assert torch.allclose(theta.grad, g2, rtol=1e-5, atol=1e-6 * float(g2.abs().max()))
+    # central differences of the GPU energy along a few coordinates
+    rng = np.random.default_rng(0)
+    h = 1e-3
+    for _ in range(4):
+        a, k = int(rng.integers(sysd.n_atoms)), int(rng.integers(3))
+        c = int(cfg[a])
+        p1, p2 = pos.detach().clone(), pos.detach().clone()
+        p1[a, k] += h
+        p2[a, k] -= h
+        with torch.no_grad():
+            d = (energy(p1, theta, pot, sysd)[c] - energy(p2, theta, pot, sysd)[c]).item() / (2 * h)
+        scale = max(rms, abs(ref["F"][a, k]))
+        assert abs(d + ref["F"][a, k]) <= 2e-3 * scale, (a, k, d, ref["F"][a, k])

@@ -180,10 +180,12 @@ def test_bad_species_is_reported(torch_cuda):
     assert torch.isfinite(F).all()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+VARIANTS = [0, 1, 2, 3, 4]   # blocked, flattened, compensated with 32 / 16 / 8 lanes per unit
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_results_are_deterministic(torch_cuda, variant):
-    # descriptors and energies bit for bit with blocked (0) and flattened (1) descriptor
-    # kernels.  Forces are summed over centres with atomics (F_j -= q_ij from every centre
+    # descriptors and energies bit for bit with every descriptor kernel variant.  Forces are summed over centres with atomics (F_j -= q_ij from every centre
     # i), so they and the training gradient that depends on them agree to rounding only.
     torch = torch_cuda
     wl = W.make("water512")
@@ -205,8 +207,30 @@ def test_results_are_deterministic(torch_cuda, variant):
     assert (g1 - g2).abs().max().item() <= 1e-5 * g1.abs().max().item()
 
 
-@pytest.mark.parametrize("name", ["molecules16", "fcc256", "ragged8", "tiny_cell"])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_descriptor_variants(torch_cuda, name, variant):
+    torch = torch_cuda
+    wl = _special(name)
+    pot = P.Potential(wl.desc, wl.archs)
+    P.panna_set_tuning(pot.ctx, "descriptor", variant)
+    sysd = P.DeviceSystem(wl.system)
+    theta = torch.as_tensor(wl.theta, dtype=torch.float32, device="cuda")
+    # panna_descriptors (rows in atom order) and the energy path (rows in network order)
+    G = pot.descriptors(sysd).cpu().numpy().astype(np.float64)
+    Go = O.workload_batch(wl, want_G=True)["G"]
+    err = H.descriptor_error(G, Go, wl.desc)
+    E = pot.energy_forces(sysd, theta, P.PANNA_MLP_FP32)[1].cpu().numpy().astype(np.float64)
+    ref = O.batch(wl.system, wl.desc, wl.archs, wl.theta.astype(np.float32).astype(np.float64))
+    aerr = float(np.abs(E - ref["E_atom"]).max() / (np.abs(ref["E_atom"]).max() + 1e-30))
+    print("%s descriptor variant %d: G err %.3g, atomic energies %.3g" % (name, variant, err, aerr))
+    assert err <= H.TOL_G
+    assert aerr <= 10 * H.TOL_E
+
+
+@pytest.mark.parametrize("name", ["molecules16", "fcc256", "ragged8", "tiny_cell", "water512", "diamond64",
+                                  "triclinic", "mixed_pbc", "edges"])
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_adjoint_and_descriptor_variants(torch_cuda, name, variant):
     torch = torch_cuda
     wl = _special(name)
@@ -226,11 +250,13 @@ def test_adjoint_and_descriptor_variants(torch_cuda, name, variant):
     verr = float(np.abs(V.cpu().numpy() - ref["virial"]).max() / (np.abs(ref["virial"]).max() + 1e-30))
     assert verr <= 10 * H.TOL_F_FP32
     aerr = float(np.abs(Ea.cpu().numpy() - ref["E_atom"]).max() / (np.abs(ref["E_atom"]).max() + 1e-30))
+    print("%s adjoint/descriptor variant %d: max|dF|/rms %.3g, virial %.3g" % (
+        name, variant, H.force_error(Fn, ref["F"])[0] if rms > 0 else 0.0, verr))
     assert aerr <= 10 * H.TOL_E
 
 
 @pytest.mark.parametrize("name", ["molecules16", "ragged8", "diamond64", "water512"])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_jvp_variants_training_gradient(torch_cuda, name, variant):
     torch = torch_cuda
     wl = W.make(name)
