@@ -241,3 +241,170 @@ class SlabPlan:
         covered by the shell of width rc + skin."""
         d = np.sqrt(((np.asarray(pos_now) - self._pos_ref) ** 2).sum(1))
         return bool(d.max(initial=0.0) <= self.skin / 2)
+
+
+class LocalSlabPlan:
+    """The slab decomposition of SlabPlan, planned by every rank from its own atoms only.
+
+    No rank holds the global positions: rank r is given the atoms it owns (those whose
+    fractional coordinate along a3, folded into [0, 1) on a periodic a3, lies in
+    [bounds3[r], bounds3[r + 1])), with their global indices and species.  Construction is
+    collective over ``group``:
+
+      1. each rank finds, among its own atoms and their images m along a3, those within
+         w = (rc + skin) / h3 (fractional) of another slab (or of its own slab, through an
+         image, when slabs are thinner than w): its send lists, one per destination rank,
+         ordered by (global index, image);
+      2. one all-to-all of the counts, one of (global index, species, image) records and one of
+         the positions builds every rank's ghosts, ordered by owning rank, then as sent.
+
+    ``halo`` refreshes the ghost positions from their owners and ``reverse`` returns the ghost
+    forces to them (all-to-all exchanges of packed device tensors: index_select on the sender,
+    index_add on the receiver); the rank's local system, ghost flags and exchange lists have
+    the layout of SlabPlan's LocalDomain, so a rank's results equal those of the global plan.
+    """
+
+    def __init__(self, rank: int, world: int, cell, pbc, rc: float, skin: float, pos_owned: np.ndarray,
+                 species_owned: np.ndarray, gid_owned: np.ndarray, bounds3: np.ndarray, n_species: int, group=None):
+        import torch
+        import torch.distributed as dist
+        cell = np.asarray(cell, np.float64).reshape(3, 3)
+        det = float(np.linalg.det(cell))
+        if abs(det) < 1e-12:
+            raise ValueError("slab decomposition needs a non-singular cell")
+        self.rank, self.world = int(rank), int(world)
+        self.cell = cell
+        self.pbc = np.asarray(pbc, np.uint8).reshape(3).copy()
+        self.rc, self.skin = float(rc), float(skin)
+        self.bounds3 = np.asarray(bounds3, np.float64)
+        a3 = cell[2]
+        h3 = abs(det) / float(np.linalg.norm(np.cross(cell[0], cell[1])))
+        w = (rc + skin) / h3
+        pos = np.asarray(pos_owned, np.float64).reshape(-1, 3)
+        s3 = (pos @ np.linalg.inv(cell))[:, 2] if len(pos) else np.zeros(0)
+        if self.pbc[2]:
+            fold = np.floor(s3)
+            f = s3 - fold
+            wrap = f >= 1.0
+            f[wrap] -= 1.0
+            fold[wrap] += 1.0
+        else:
+            fold = np.zeros_like(s3)
+            f = s3.copy()
+        lo_r, hi_r = self.bounds3[rank], self.bounds3[rank + 1]
+        if np.any((f < lo_r) | (f >= hi_r)) and not (rank == world - 1 and np.all(f <= hi_r)):
+            raise ValueError("rank %d was given atoms outside its slab" % rank)
+        self.pos_folded = pos - fold[:, None] * a3[None, :]
+        self._pos_ref = pos.copy()
+        self.gid = np.asarray(gid_owned, np.int64)
+        spec = np.asarray(species_owned, np.int32)
+        M = int(math.ceil(w)) + 1 if self.pbc[2] else 0
+        # 1. send lists
+        send_rows, send_img = [], []
+        for q in range(world):
+            lo, hi = self.bounds3[q], self.bounds3[q + 1]
+            rows, imgs = [], []
+            for m in range(-M, M + 1):
+                fm = f + m
+                sel = ((fm >= lo - w) & (fm < lo)) | ((fm >= hi) & (fm < hi + w))
+                idx = np.nonzero(sel)[0]
+                rows.append(idx)
+                imgs.append(np.full(idx.size, m, np.int64))
+            rows = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+            imgs = np.concatenate(imgs) if imgs else np.zeros(0, np.int64)
+            order = np.lexsort((imgs, self.gid[rows]))
+            send_rows.append(rows[order].astype(np.int64))
+            send_img.append(imgs[order])
+        self.send_idx = send_rows
+        # 2. exchanges: counts, records, positions
+        scount = torch.tensor([len(r) for r in send_rows], dtype=torch.int64)
+        rcount = torch.empty(world, dtype=torch.int64)
+        dist.all_to_all_single(rcount, scount, group=group)
+        self.recv_counts = rcount.numpy().astype(np.int64)
+        rec = np.concatenate([np.stack([self.gid[r], spec[r].astype(np.int64), m], 1)
+                              for r, m in zip(send_rows, send_img)]) if world else np.zeros((0, 3), np.int64)
+        rrec = torch.empty((int(self.recv_counts.sum()), 3), dtype=torch.int64)
+        dist.all_to_all_single(rrec, torch.as_tensor(rec.reshape(-1, 3)), [int(k) for k in self.recv_counts],
+                               [len(r) for r in send_rows], group=group)
+        rrec = rrec.numpy()
+        self.ghost_src, ghost_spec, self.ghost_img = rrec[:, 0].copy(), rrec[:, 1].astype(np.int32), rrec[:, 2].copy()
+        gpos = self.halo_numpy(self.pos_folded, group)
+        n_own = len(pos)
+        pbc_l = self.pbc.copy()
+        pbc_l[2] = 0
+        loc = np.concatenate([self.pos_folded, gpos])
+        self.system = System(np.array([0, len(loc)], np.int64), loc, np.concatenate([spec, ghost_spec]),
+                             cell.reshape(1, 9).copy(), pbc_l.reshape(1, 3), n_species)
+        self.ghost = np.concatenate([np.zeros(n_own, np.uint8), np.ones(len(gpos), np.uint8)])
+        self.n_owned = n_own
+
+    def halo_numpy(self, x_owned: np.ndarray, group=None) -> np.ndarray:
+        """Ghost positions (owners' folded positions plus the image shifts) as a numpy array."""
+        import torch
+        out = self._exchange_forward(torch.as_tensor(np.asarray(x_owned, np.float64)), group)
+        return out.numpy()
+
+    def _exchange_forward(self, x_owned, group=None):
+        import torch
+        import torch.distributed as dist
+        rows = torch.as_tensor(np.concatenate(self.send_idx) if self.send_idx else np.zeros(0, np.int64),
+                               device=x_owned.device)
+        sbuf = x_owned.index_select(0, rows).contiguous()
+        rbuf = torch.empty((int(self.recv_counts.sum()), 3), dtype=x_owned.dtype, device=x_owned.device)
+        dist.all_to_all_single(rbuf, sbuf, [int(k) for k in self.recv_counts], [len(s) for s in self.send_idx],
+                               group=group)
+        a3 = torch.as_tensor(self.cell[2], dtype=x_owned.dtype, device=x_owned.device)
+        img = torch.as_tensor(self.ghost_img, dtype=x_owned.dtype, device=x_owned.device)
+        return rbuf + img[:, None] * a3[None, :]
+
+    def halo(self, x_owned, group=None):
+        """Forward halo exchange: this rank's folded positions [n_owned, 3] (a tensor on any
+        device) -> local positions [n_local, 3], owned rows then ghosts."""
+        import torch
+        return torch.cat([x_owned, self._exchange_forward(x_owned, group)])
+
+    def reverse(self, F_local, group=None):
+        """Reverse halo exchange: local forces [n_local, 3] -> complete forces on the owned atoms."""
+        import torch
+        import torch.distributed as dist
+        n = self.n_owned
+        sbuf = F_local[n:].contiguous()
+        counts = [len(s) for s in self.send_idx]
+        rbuf = torch.empty((sum(counts), 3), dtype=F_local.dtype, device=F_local.device)
+        dist.all_to_all_single(rbuf, sbuf, counts, [int(k) for k in self.recv_counts], group=group)
+        out = F_local[:n].clone()
+        rows = torch.as_tensor(np.concatenate(self.send_idx) if self.send_idx else np.zeros(0, np.int64),
+                               device=F_local.device)
+        out.index_add_(0, rows, rbuf)
+        return out
+
+    def still_valid(self, pos_now: np.ndarray, group=None) -> bool:
+        """True on every rank while no atom of any rank has moved more than skin/2 since the
+        plan was built (one all-reduce of the largest local displacement)."""
+        import torch
+        import torch.distributed as dist
+        d = np.sqrt(((np.asarray(pos_now) - self._pos_ref) ** 2).sum(1))
+        t = torch.tensor([float(d.max(initial=0.0))], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+        return bool(t.item() <= self.skin / 2)
+
+
+def periodic_slab_bounds(world: int) -> np.ndarray:
+    """Equal fractional slabs along a periodic a3: rank r owns [r / world, (r + 1) / world)."""
+    return np.arange(world + 1, dtype=np.float64) / world
+
+
+def owned_by_slab(system: System, bounds3: np.ndarray, rank: int) -> np.ndarray:
+    """Indices of the atoms of a one-configuration system that rank ``rank`` owns under the
+    slab bounds (folded fractional coordinate along a periodic a3): the initial distribution
+    of atoms to ranks, after which each rank keeps only its own."""
+    cell = system.cell[0].reshape(3, 3)
+    s3 = (system.pos @ np.linalg.inv(cell))[:, 2]
+    if system.pbc[0, 2]:
+        f = s3 - np.floor(s3)
+        f[f >= 1.0] -= 1.0
+    else:
+        f = s3
+    world = len(bounds3) - 1
+    owner = np.clip(np.searchsorted(bounds3, f, side="right") - 1, 0, world - 1)
+    return np.nonzero(owner == rank)[0]

@@ -202,3 +202,64 @@ def test_gloo_two_ranks_slabs_and_data_parallel_training():
     port = _free_port()
     mp.start_processes(_rank_main, args=(2, port, errors), nprocs=2, join=True, start_method="spawn")
     assert errors.empty()
+
+
+# ------------------------------------------------------------------ locally planned slabs
+
+def _local_rank_main(rank, world, port, errors):
+    import torch
+    import torch.distributed as dist
+    try:
+        os.environ["MASTER_ADDR"] = "127.0.0.1"
+        os.environ["MASTER_PORT"] = str(port)
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+        wl = W.make("fcc256")
+        sysg = _triclinic(wl.system)
+        bounds = Dm.periodic_slab_bounds(world)
+        # the initial distribution: this rank keeps only its own atoms
+        own = Dm.owned_by_slab(sysg, bounds, rank)
+        plan = Dm.LocalSlabPlan(rank, world, sysg.cell[0], sysg.pbc[0], wl.desc.rc, 0.3, sysg.pos[own],
+                                sysg.species[own], own, bounds, sysg.n_species)
+        # the same ghosts and local layout as the plan built from the global positions
+        ref_plan = Dm.SlabPlan(sysg, wl.desc.rc, world, skin=0.3)
+        d = ref_plan.domains[rank]
+        np.testing.assert_array_equal(plan.gid, d.owned)
+        np.testing.assert_array_equal(plan.recv_counts, d.recv_counts)
+        got = np.stack([plan.ghost_src, plan.ghost_img], 1)
+        want = np.stack([d.ghost_src, d.ghost_img], 1)
+        np.testing.assert_array_equal(got, want)
+        np.testing.assert_allclose(plan.system.pos, d.system.pos, rtol=0, atol=1e-12)
+        # a displacement refreshed through the halo, then forces back to their owners
+        x = torch.as_tensor(plan.pos_folded + 1e-3 * np.sin(np.arange(3 * plan.n_owned)).reshape(-1, 3))
+        x_local = plan.halo(x)
+        moved = dataclasses.replace(sysg, pos=sysg.pos.copy())
+        moved.pos[own] = x.numpy()
+        # every rank's moved atoms are needed for the whole-configuration reference
+        allx = [torch.zeros(0)] * world
+        dist.all_gather_object(allx, (own, x.numpy()))
+        for o, xx in allx:
+            moved.pos[o] = xx
+        loc = dataclasses.replace(plan.system, pos=x_local.numpy())
+        part = O.batch(loc, wl.desc, wl.archs, wl.theta, ghost=plan.ghost)
+        F_own = plan.reverse(torch.as_tensor(part["F"])).numpy()
+        ref = O.batch(moved, wl.desc, wl.archs, wl.theta)
+        assert np.abs(F_own - ref["F"][own]).max() < 1e-12 * np.abs(ref["F"]).max(), "forces"
+        e = torch.tensor([part["E_cfg"][0]], dtype=torch.float64)
+        dist.all_reduce(e)
+        assert abs(e.item() - ref["E_cfg"][0]) < 1e-12 * np.abs(ref["E_atom"]).sum(), "energy"
+        assert plan.still_valid(x.numpy())
+        dist.barrier()
+        dist.destroy_process_group()
+    except Exception as e:
+        errors.put("rank %d: %r" % (rank, e))
+        raise
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_locally_planned_slabs(world):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    errors = ctx.SimpleQueue()
+    port = _free_port()
+    mp.start_processes(_local_rank_main, args=(world, port, errors), nprocs=world, join=True, start_method="spawn")
+    assert errors.empty()
