@@ -196,7 +196,10 @@ int32_t panna_neighbor_capacity(const panna_ctx* ctx);
 panna_status panna_set_async(panna_ctx* ctx, int32_t async);
 
 /*
- * Arithmetic of the angular descriptor terms (descriptor, adjoint, JVP):
+ * Arithmetic of the angular descriptor terms in kernel variants 0 and 1 (descriptor, adjoint,
+ * JVP; the compensated variants 2..4 always evaluate the angle from the cross product of the
+ * FP32 relative vectors, t_m = 1 - y_m from the half angles and y^zeta from a series of
+ * log(1 - t), which is about as accurate as the extended mode below at plain-FP32 cost):
  *   0 = automatic (default): extended precision for the descriptor and the adjoint with FP32
  *       networks (force tolerance 1e-5 of RMS), plain FP32 with the BF16 modes (their
  *       tolerance is 1e-2) and for the JVP of the weight gradient (tolerance 1e-4);
@@ -215,18 +218,27 @@ panna_status panna_set_angular_precision(panna_ctx* ctx, int32_t mode);
  * knobs "descriptor", "adjoint", "jvp" (the three kernels over angular pairs): -1 (default)
  * = tuned, 0 = pairs by species block (8 warps per CTA), 1 = all pairs of an atom in one
  * flattened range (4 warps per CTA; shared-memory atomics make the sums reproducible to
- * rounding rather than bit for bit).  knob "mlp_fp32" (PANNA_MLP_FP32 networks): a bit mask of the first layer's
+ * rounding rather than bit for bit), 2 / 3 / 4 = the compensated-FP32 kernels with 32 / 16 / 8
+ * lanes per unit of pairs (resident warps walking the atoms; packed two-wide FP32 arithmetic).
+ * Without autotuning, batches of at least 1216 atoms take variant 2 and smaller ones variant 0
+ * (several warps per atom).  knob "mlp_fp32" (PANNA_MLP_FP32 networks): a bit mask of the first layer's
  * products (descriptor width to first hidden width, almost all of the networks'
  * arithmetic) that run on the tensor cores with operands split into TF32 parts, the rest
- * staying on the CUDA cores in plain FP32: 1 = forward (three parts), 2 = input gradient
- * dE/dG (three parts), 4 = tangent of the weight-gradient pass (two parts), 8 = weight
- * gradient (two parts).  Default 4 | 8 = 12: the training-only products, so that energies
+ * staying on the CUDA cores in plain FP32: 1 = forward (three parts), 4 = tangent of the
+ * weight-gradient pass (two parts), 8 = weight gradient (two parts); bit 2 (the input
+ * gradient, whose forces sat at the 1e-5 bar rather than within it) is not accepted.  Default 4 | 8 = 12: the training-only products, so that energies
  * and forces are those of the plain FP32 path; the tensor cores' accumulation makes the
  * forward product about 6x less accurate than an FP32 dot product rounded to nearest.
  * 0 = everything on the CUDA cores.  Returns PANNA_ERR_INVALID_ARG for an unknown knob or
  * value.
  */
 panna_status panna_set_tuning(panna_ctx* ctx, const char* knob, int32_t value);
+
+/* The kernel variant that knob "descriptor", "adjoint" or "jvp" ran with in the last compute
+ * call that used it (tuned or forced): 0 blocked, 1 flattened, 2 / 3 / 4 compensated with 32 / 16
+ * / 8 lanes per (species block, theta chunk, R chunk) unit; -1 before any such call or for an
+ * unknown knob. */
+int32_t panna_tuning_choice(const panna_ctx* ctx, const char* knob);
 
 /*
  * Langevin dynamics (the MD loop the paper times on a 16-atom carbon cell, Sec. III.B;
@@ -569,6 +581,11 @@ float panna_stage_ms(const panna_ctx* ctx, const char* stage);
  * The paper has no counterpart: this is the denominator of the kernels' reported efficiency.
  */
 panna_status panna_measure_alu_peaks(double* fp32_tflops, double* ex2_gops, panna_stream_t stream);
+
+/* As panna_measure_alu_peaks, plus *fp32x2_tflops (host): the same FMA chains issued as packed
+ * two-wide FP32 FMAs (one instruction per two FMAs), which the angular kernels use. */
+panna_status panna_measure_alu_peaks2(double* fp32_tflops, double* fp32x2_tflops, double* ex2_gops,
+                                      panna_stream_t stream);
 
 /*
  * Descriptors G [n_atoms*D] FP32 (device, row i = atom i) of a small batch, computed

@@ -86,6 +86,7 @@ struct panna_ctx {
     LossOpts loss_opts{0, 0, 0, 0.0, 0.0};
     bool frozen[kMaxSpecies][kMaxLayers] = {};
     int last_launches = 0;
+    int last_variant[3] = {-1, -1, -1};   // descriptor, adjoint, JVP variants of the last call
     DescGrid64 g64{};                 // FP64 descriptor parameters (stored Jacobians)
     QeqDev qeq{};                     // charge-equilibration constants (3-output networks)
     bool qeq_set = false;
@@ -144,7 +145,7 @@ constexpr int kSplits = 16;
 int tf32_mask(const panna_ctx* c, bool bf16, bool train)
 {
     if (bf16 || !tf32_first_layer_ok(c->plan)) return 0;
-    return c->fp32_tc & (train ? (TF32_FWD | TF32_INGRAD | TF32_TAN | TF32_WGRAD) : (TF32_FWD | TF32_INGRAD));
+    return c->fp32_tc & (train ? (TF32_FWD | TF32_TAN | TF32_WGRAD) : TF32_FWD);
 }
 
 void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, Layout& L, int cap_c = 0)
@@ -366,7 +367,18 @@ ParamRanges frozen_ranges(const panna_ctx* c)
 enum { KV_DESC = 0, KV_ADJ = 1, KV_JVP = 2 };
 
 template <class Launch>
+int tuned_variant_(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch);
+
+template <class Launch>
 int tuned_variant(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch)
+{
+    const int v = tuned_variant_(c, sys, prec, kind, s, launch);
+    c->last_variant[kind] = v;
+    return v;
+}
+
+template <class Launch>
+int tuned_variant_(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch)
 {
     if (c->force_variant[kind] >= 0) return c->force_variant[kind];
     panna_ctx::Tuned* t = nullptr;
@@ -472,11 +484,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         CU(mlp_energy_rows(c->plan, L.mb, N, L.E_rows, s, &nl));
     }
     if (need_forces) {
-        if (tf && (tfm & TF32_INGRAD)) {
-            float* ab1 = nullptr;
-            CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl, &ab1));
-            CU(tf32_input_grad1(c->plan, L.mb, N, L.tf_ws, tfm, ab1, L.g, L.w.status, s, &nl));
-        } else if (!tc) {
+        if (!tc) {
             CU(mlp_input_grad(c->plan, L.mb, rq.theta, N, L.g, s, &nl));
         }
         stage_mark(c, 3, s);
@@ -729,6 +737,15 @@ panna_status panna_set_angular_precision(panna_ctx* c, int32_t mode)
     return PANNA_OK;
 }
 
+int32_t panna_tuning_choice(const panna_ctx* c, const char* knob)
+{
+    if (!c || !knob) return -1;
+    const char* kinds[3] = {"descriptor", "adjoint", "jvp"};
+    for (int k = 0; k < 3; ++k)
+        if (strcmp(knob, kinds[k]) == 0) return c->last_variant[k];
+    return -1;
+}
+
 panna_status panna_set_tuning(panna_ctx* c, const char* knob, int32_t value)
 {
     if (!c || !knob) return fail(PANNA_ERR_INVALID_ARG, "null argument");
@@ -743,7 +760,7 @@ panna_status panna_set_tuning(panna_ctx* c, const char* knob, int32_t value)
             c->force_variant[k] = value;
             return PANNA_OK;
         }
-    if (strcmp(knob, "mlp_fp32") == 0 && value >= 0 && value <= 15) {
+    if (strcmp(knob, "mlp_fp32") == 0 && value >= 0 && value <= 15 && !(value & 2)) {
         c->fp32_tc = value;
         return PANNA_OK;
     }

@@ -48,6 +48,7 @@ struct DescDev {
     float sin_half_t[kMaxTheta];
     float zpoly[5];                // zeta log2(e) log(y) = w (c0 + c1 w^2 + ... + c4 w^8), w = t / (2 - t)
     float rs_ang_step;             // dR of a uniform angular R grid, else 0
+    float cos_t[kMaxTheta], sin_t[kMaxTheta];   // cos(theta_m), sin(theta_m)
     // standard BP angular term (ang_kind 1): sector m = (lambda_m, zeta_m), shell n = eta_n
     int32_t ang_kind;              // 0 = modified (mBP), 1 = standard BP
     float bp_lambda[kMaxTheta], bp_zeta[kMaxTheta], bp_pref[kMaxTheta];   // pref = 2^(1 - zeta)

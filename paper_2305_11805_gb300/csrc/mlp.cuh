@@ -74,11 +74,11 @@ cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
                            bool tan_tc = false, const WgradTc* wtc = nullptr, MlpGradPart part = MLP_GRAD_ALL);
 
 // FP32 networks with the first layer on the tensor cores as TF32 hi + lo pairs (mlp_tc.cu).
-// Order per call: tf32_prepare, tf32_forward1, mlp_forward(l0 = 1); mlp_input_grad(ab1) and
-// tf32_input_grad1; for training tf32_tangent1, then mlp_param_grad(tan_tc, wtc), which calls
-// tf32_wgrad for every layer.
+// Order per call: tf32_prepare, tf32_forward1, mlp_forward(l0 = 1); mlp_input_grad; for
+// training tf32_tangent1, then mlp_param_grad(tan_tc, wtc), which calls tf32_wgrad for every
+// layer.
 // Each of the four products may also stay on the CUDA cores (TF32_* bits below).
-enum { TF32_FWD = 1, TF32_INGRAD = 2, TF32_TAN = 4, TF32_WGRAD = 8 };
+enum { TF32_FWD = 1, TF32_INGRAD = 2, TF32_TAN = 4, TF32_WGRAD = 8 };   // TF32_INGRAD: not offered
 bool tf32_first_layer_ok(const MlpPlan& p);
 // mask: the TF32_* products used in this evaluation (the same value in every call of one evaluation)
 size_t tf32_workspace_bytes(const MlpPlan& p, int64_t N, int mask);
@@ -86,8 +86,6 @@ cudaError_t tf32_prepare(const MlpPlan& p, const MlpBuffers& b, const float* the
                          cudaStream_t s, int* launches);
 cudaError_t tf32_forward1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, DevStatus* status,
                           cudaStream_t s, int* launches);
-cudaError_t tf32_input_grad1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, const float* Ab1,
-                             float* g, DevStatus* status, cudaStream_t s, int* launches);
 cudaError_t tf32_tangent1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, const float* Gdot,
                           DevStatus* status, cudaStream_t s, int* launches);
 // weight gradient of layer l+1 from b.Zb, b.Zdb (its adjoints) and its inputs A, Ad

@@ -503,24 +503,6 @@ __global__ void k_split_tf32(int64_t rows, int cols, int lds, int ldo, const flo
     store_split_tf32(o.p[0], o.p[1], o.p[2], (size_t)i, c < cols ? x[(size_t)r * lds + c] : 0.f);
 }
 
-// zbar_1 = abar_1 * act'(Z_1) as TF32 parts (row stride ldo); 0 outside the species' width
-// and on rows past the last species
-__global__ void k_dact_split_tf32(int64_t N, int ld, int ldo, LayerArgs la, const int32_t* __restrict__ seg_off,
-                                  const float* __restrict__ Ab, const float* __restrict__ Z, Parts3 o)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N * ldo) return;
-    const int64_t r = i / ldo;
-    const int c = (int)(i % ldo);
-    float v = 0.f;
-    if (r < seg_off[la.S]) {
-        int s = 0;
-        while (s < la.S - 1 && r >= seg_off[s + 1]) ++s;
-        if (c < la.N[s]) v = Ab[(size_t)r * ld + c] * act_d1(la.act[s], Z[(size_t)r * ld + c]);
-    }
-    store_split_tf32(o.p[0], o.p[1], o.p[2], (size_t)i, v);
-}
-
 // Padded atom columns for the weight gradient: species s owns columns
 // pstart[s] .. pstart[s] + round_up(n_s, 32) - 1, cut into items of `chunk` columns.
 __global__ void k_tf32_items(int S, const int32_t* __restrict__ seg_off, int chunk, int32_t* __restrict__ pstart,
@@ -1456,29 +1438,6 @@ cudaError_t tf32_forward1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void
     ta.outF = b.Z[1]; ta.ldF = p.ld[1];
     ta.outA = b.A[1]; ta.ldA = p.ld[1];
     e = launch_tc<TC_FWD32, kPartsFwd, true>(m, ta, N, p.ld[1], s);
-    ++*launches;
-    return e;
-}
-
-// g = (abar_1 * act'(Z_1)) W_1 (FP32 out); Ab1 = dE/dA_1 with row stride ld[1]
-cudaError_t tf32_input_grad1(const MlpPlan& p, const MlpBuffers& b, int64_t N, void* ws, int mask, const float* Ab1,
-                             float* g, DevStatus* status, cudaStream_t s, int* launches)
-{
-    Tf32Bufs t;
-    tf32_carve(p, N, mask, static_cast<char*>(ws), t);
-    const int D = p.ld[0], h1 = p.ld[1];
-    LayerArgs la = tc_layer_args(p, 0);
-    k_dact_split_tf32<<<blocks(N * t.ldz), 256, 0, s>>>(N, h1, t.ldz, la, b.seg_off, Ab1, b.Z[1],
-                                                        parts_of(t.Zb, kPartsFwd));
-    ++*launches;
-    TcMaps m;
-    cudaError_t e = tf32_maps(m, kPartsFwd, t.Zb, N, h1, t.ldz, kTcBM, t.Wb, (int64_t)p.S * t.npb, h1, t.kpb, t.bnb);
-    if (e != cudaSuccess) return e;
-    TcArgs ta = tf32_base(p, b, t, status);
-    for (int q = 0; q < p.S; ++q) ta.N[q] = p.widths[q][0];
-    ta.K = h1; ta.BN = t.bnb; ta.n_pad = t.npb;
-    ta.outF = g; ta.ldF = D;
-    e = launch_tc<TC_BWD_OUT, kPartsFwd, true>(m, ta, N, D, s);
     ++*launches;
     return e;
 }

@@ -36,6 +36,25 @@ __global__ void __launch_bounds__(kPeakThreads) k_fma_peak(float* out, int iters
     if (s == 1234.5f) out[blockIdx.x] = s;   // keeps the chains live; practically never taken
 }
 
+// the same chains with packed two-wide FP32 FMAs (one instruction, two FMAs per lane)
+__global__ void __launch_bounds__(kPeakThreads) k_fma2_peak(float* out, int iters, float a, float b)
+{
+    float2 x[kChains / 2];
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k) x[k] = make_float2(1e-3f * (float)threadIdx.x + (float)k, (float)k - 1.f);
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int k = 0; k < kChains / 2; ++k) x[k] = __ffma2_rn(x[k], a2, b2);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k) s += x[k].x + x[k].y;
+    if (s == 1234.5f) out[blockIdx.x] = s;
+}
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -63,9 +82,19 @@ __global__ void __launch_bounds__(kPeakThreads) k_ex2_peak(float* out, int iters
 
 }  // namespace
 
+extern "C" panna_status panna_measure_alu_peaks2(double* fp32_tflops, double* fp32x2_tflops, double* ex2_gops,
+                                                 panna_stream_t stream);
+
 extern "C" panna_status panna_measure_alu_peaks(double* fp32_tflops, double* ex2_gops, panna_stream_t stream)
 {
-    if (!fp32_tflops || !ex2_gops) {
+    double packed = 0.0;
+    return panna_measure_alu_peaks2(fp32_tflops, &packed, ex2_gops, stream);
+}
+
+extern "C" panna_status panna_measure_alu_peaks2(double* fp32_tflops, double* fp32x2_tflops, double* ex2_gops,
+                                                 panna_stream_t stream)
+{
+    if (!fp32_tflops || !fp32x2_tflops || !ex2_gops) {
         panna::set_last_error_message("null argument");
         return PANNA_ERR_INVALID_ARG;
     }
@@ -81,7 +110,7 @@ extern "C" panna_status panna_measure_alu_peaks(double* fp32_tflops, double* ex2
     const unsigned blocks = (unsigned)(n_sm * kPeakBlocksPerSm);
     const double threads = (double)blocks * kPeakThreads;
     const int fma_iters = 20000, ex2_iters = 2000;
-    double best_fma = 0.0, best_ex2 = 0.0;
+    double best_fma = 0.0, best_ex2 = 0.0, best_fma2 = 0.0;
     for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
         float ms = 0.f;
         e = cudaEventRecord(t0, s);
@@ -95,6 +124,18 @@ extern "C" panna_status panna_measure_alu_peaks(double* fp32_tflops, double* ex2
         if (e == cudaSuccess && rep > 0 && ms > 0.f) {   // the first launch is a warm-up
             const double fl = 2.0 * threads * fma_iters * kUnroll * kChains;
             if (fl / (ms * 1e-3) / 1e12 > best_fma) best_fma = fl / (ms * 1e-3) / 1e12;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+        if (e == cudaSuccess) {
+            k_fma2_peak<<<blocks, kPeakThreads, 0, s>>>(sink, fma_iters, 0.9999999f, 1e-7f);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e == cudaSuccess && rep > 0 && ms > 0.f) {
+            const double fl = 2.0 * threads * fma_iters * kUnroll * kChains;
+            if (fl / (ms * 1e-3) / 1e12 > best_fma2) best_fma2 = fl / (ms * 1e-3) / 1e12;
         }
         if (e == cudaSuccess) e = cudaEventRecord(t0, s);
         if (e == cudaSuccess) {
@@ -122,6 +163,7 @@ extern "C" panna_status panna_measure_alu_peaks(double* fp32_tflops, double* ex2
         return PANNA_ERR_CUDA;
     }
     *fp32_tflops = best_fma;
+    *fp32x2_tflops = best_fma2;
     *ex2_gops = best_ex2;
     return PANNA_OK;
 }

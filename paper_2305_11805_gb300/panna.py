@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
         "panna_check": (i32, [_vp, _vp]),
         "panna_set_angular_precision": (i32, [_vp, i32]),
         "panna_set_tuning": (i32, [_vp, C.c_char_p, i32]),
+        "panna_tuning_choice": (i32, [_vp, C.c_char_p]),
         "panna_set_loss_normalization": (i32, [_vp, i64, i64]),
         "panna_set_loss_options": (i32, [_vp, C.POINTER(panna_loss_options)]),
         "panna_set_frozen": (i32, [_vp, i32, i32, i32]),
@@ -128,6 +129,7 @@ def load(path: str = LIB_PATH):
         "panna_stage_ms": (f32, [_vp, C.c_char_p]),
         "panna_descriptors_static": (i32, [C.POINTER(panna_desc_params), C.POINTER(panna_system), _vp, _vp]),
         "panna_measure_alu_peaks": (i32, [C.POINTER(f64), C.POINTER(f64), _vp]),
+        "panna_measure_alu_peaks2": (i32, [C.POINTER(f64), C.POINTER(f64), C.POINTER(f64), _vp]),
         "panna_capture": (i32, [_vp, C.POINTER(panna_system), _vp, i32, _vp, _vp, _vp, _vp, _vp]),
         "panna_replay": (i32, [_vp, _vp]),
         "panna_set_qeq": (i32, [_vp, C.POINTER(panna_qeq_params)]),
@@ -153,11 +155,11 @@ def load(path: str = LIB_PATH):
 def exported_symbols() -> Sequence[str]:
     return ["panna_version", "panna_last_error", "panna_descriptor_size", "panna_create", "panna_destroy",
             "panna_param_count", "panna_set_neighbor_capacity", "panna_neighbor_capacity", "panna_set_async",
-            "panna_check", "panna_set_angular_precision", "panna_set_tuning", "panna_set_loss_normalization",
+            "panna_check", "panna_set_angular_precision", "panna_set_tuning", "panna_tuning_choice", "panna_set_loss_normalization",
             "panna_md_run", "panna_set_loss_options", "panna_set_frozen", "panna_adam_step",
             "panna_neighbors", "panna_descriptors", "panna_energy_forces", "panna_param_vjp",
             "panna_loss_grad", "panna_last_launch_count", "panna_set_profiling", "panna_stage_ms",
-            "panna_descriptors_static", "panna_measure_alu_peaks", "panna_capture", "panna_replay", "panna_store_plan",
+            "panna_descriptors_static", "panna_measure_alu_peaks", "panna_measure_alu_peaks2", "panna_capture", "panna_replay", "panna_store_plan",
             "panna_store_sections", "panna_store_build", "panna_store_energy_forces", "panna_store_loss_grad",
             "panna_set_qeq", "panna_qeq_energy_forces", "panna_qeq_loss_grad"]
 
@@ -264,6 +266,10 @@ def panna_set_tuning(ctx: int, knob: str, value: int):
     _check(load().panna_set_tuning(ctx, knob.encode(), int(value)))
 
 
+def panna_tuning_choice(ctx: int, knob: str) -> int:
+    return int(load().panna_tuning_choice(ctx, knob.encode()))
+
+
 def panna_set_loss_normalization(ctx: int, n_cfg_total: int, n_atoms_total: int):
     _check(load().panna_set_loss_normalization(ctx, int(n_cfg_total), int(n_atoms_total)))
 
@@ -357,6 +363,13 @@ def panna_measure_alu_peaks(stream=None):
     a, b = C.c_double(0.0), C.c_double(0.0)
     _check(load().panna_measure_alu_peaks(C.byref(a), C.byref(b), _stream(stream)))
     return float(a.value), float(b.value)
+
+
+def panna_measure_alu_peaks2(stream=None):
+    """(FP32 FMA TFLOP/s scalar, packed two-wide, ex2 G results/s) measured now."""
+    a, b, c = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+    _check(load().panna_measure_alu_peaks2(C.byref(a), C.byref(b), C.byref(c), _stream(stream)))
+    return float(a.value), float(b.value), float(c.value)
 
 
 def panna_capture(ctx: int, sysd: "DeviceSystem", theta, prec: int, E_cfg, E_atom, F, virial, stream=None):

@@ -68,13 +68,11 @@ def test_descriptors_match_oracle(torch_cuda, name):
     assert err <= H.TOL_G
 
 
-# FP32 networks: the first layer's products on the tensor cores as TF32 parts (bit mask:
-# 1 forward, 2 input gradient, 4 tangent, 8 weight gradient; 12 is the default) or
-# everything on the CUDA cores (0).  The default and the all-CUDA-core path must meet the
-# FP32 tolerances.  The opt-in path 2 | 12 (input gradient on the tensor cores as well) sits
-# at the force bar (measured 0.9-1.02e-5 of RMS on water512) and is held to 2e-5 instead.
-FP32_PATHS = [12, 0, 14]
-FORCE_BOUND = {12: H.TOL_F_FP32, 0: H.TOL_F_FP32, 14: 2 * H.TOL_F_FP32}
+# FP32 networks: the training products of the first layer on the tensor cores as TF32 parts
+# (bit mask: 1 forward, 4 tangent, 8 weight gradient; 12 is the default) or everything on the
+# CUDA cores (0).  Both must meet the FP32 tolerances.
+FP32_PATHS = [12, 0]
+FORCE_BOUND = {12: H.TOL_F_FP32, 0: H.TOL_F_FP32}
 
 
 @pytest.mark.parametrize("path", FP32_PATHS)
