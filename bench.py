@@ -80,11 +80,15 @@ def dist_env():
 
 TRAFFIC_FILE = "profiles/geometry_kernels_molecules1024.md"
 STORE_TRAFFIC_FILE = "profiles/store_kernels_molecules1024.md"
+RAGGED_TRAFFIC_FILE = "profiles/angular_kernels_ragged256.md"
 
 
-def measured_traffic(kernel, path=TRAFFIC_FILE):
+def measured_traffic(kernel, path=TRAFFIC_FILE, atoms=None):
     """DRAM bytes per launch of `kernel` from a committed ncu summary, or None when there is
-    none or the kernel source has changed since the counters were taken."""
+    none or the kernel source has changed since the counters were taken.  With `atoms`, the
+    summary's figure (captured on a smaller batch of the same recipe, `atoms=` in its line) is
+    scaled to that many atoms: the angular kernels read each atom's neighbour slots and its
+    descriptor or gradient row once, so their traffic grows with the atoms processed."""
     import hashlib
     try:
         with open(os.path.join(ROOT, path)) as f:
@@ -99,7 +103,13 @@ def measured_traffic(kernel, path=TRAFFIC_FILE):
     except (OSError, KeyError):
         return None
     v = kv.get("k_" + kernel)
-    return int(v) if v is not None else None
+    if v is None:
+        return None
+    if atoms is not None:
+        if "atoms" not in kv:
+            return None
+        return int(round(int(v) * atoms / int(kv["atoms"])))
+    return int(v)
 
 
 def load_peaks():
@@ -339,7 +349,10 @@ def run_infer(args):
         O.build()
         pool = OraclePool(max(1, min(host_info()[0], 64)))
 
-    wl = W.make(name, seed=args.seed + rank)
+    if name == "ragged4096" and args.n_cfg:
+        wl = W.ragged(args.seed + rank, args.n_cfg)   # the first n_cfg boxes of the same recipe
+    else:
+        wl = W.make(name, seed=args.seed + rank)
     s = wl.system
     N, C = s.n_atoms, s.n_cfg
     dev = torch.device("cuda", local)
@@ -354,7 +367,7 @@ def run_infer(args):
     small = N * wl.desc.D * 4 < 512 * 1024 * 1024     # descriptor rows alone below 4 x L2: flush
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if small else None
 
-    fp32_tflops, ex2_gops = P.panna_measure_alu_peaks()
+    fp32_tflops, fp32x2_tflops, ex2_gops = P.panna_measure_alu_peaks2()
 
     # stage times of the same call (direct calls with stage events; the graph has none)
     P.panna_energy_forces(pot.ctx, sysd, theta, prec, E, None, F, None)
@@ -469,11 +482,14 @@ def run_infer(args):
     stage_flops["mlp"] = 2 * mlp_fwd      # forward + input gradient (algorithmic, one product each)
     dom = max(("descriptor", "adjoint"), key=lambda k: stage_ms.get(k, 0.0))
     ach = stage_flops[dom] / (stage_ms[dom] * 1e-3) / 1e12
+    traffic = measured_traffic(dom, RAGGED_TRAFFIC_FILE, atoms=N) if name == "ragged4096" else None
     roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_tflops, "unit": "TFLOP/s",
-            "frac": ach / fp32_tflops, "traffic": None,
+            "frac": ach / fp32_tflops, "traffic": traffic,
+            "traffic_source": (RAGGED_TRAFFIC_FILE + " (scaled by atoms)") if traffic is not None else None,
             "peak_source": "measured in this run: FP32 FMA microbenchmark (panna_measure_alu_peaks) on all SMs",
             "derived_peak": N_SM * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12,
-            "ex2_peak_gops": ex2_gops, "ms_per_launch": stage_ms[dom],
+            "fp32x2_packed_peak": fp32x2_tflops, "ex2_peak_gops": ex2_gops, "ms_per_launch": stage_ms[dom],
+            "kernel_variant": {k: P.panna_tuning_choice(pot.ctx, k) for k in ("descriptor", "adjoint")},
             "flop_per_angular_pair": per_pair[dom], "angular_pairs": n_pairs, "neighbour_entries": n_entries,
             "stage_tflops": {k: round(stage_flops[k] / (stage_ms[k] * 1e-3) / 1e12, 3)
                              for k in stage_flops if stage_ms.get(k, 0) > 0},
@@ -1170,6 +1186,8 @@ def main():
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the FP32 one-configuration-per-call comparison (ragged4096)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(INFER) + [TRAIN, "md", "stored", "qeq"])
+    ap.add_argument("--n-cfg", type=int, default=0,
+                    help="ragged4096 only: the first N boxes of the batch (small cases for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

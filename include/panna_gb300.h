@@ -219,8 +219,12 @@ panna_status panna_set_angular_precision(panna_ctx* ctx, int32_t mode);
  * = tuned, 0 = pairs by species block (8 warps per CTA), 1 = all pairs of an atom in one
  * flattened range (4 warps per CTA; shared-memory atomics make the sums reproducible to
  * rounding rather than bit for bit), 2 / 3 / 4 = the compensated-FP32 kernels with 32 / 16 / 8
- * lanes per unit of pairs (resident warps walking the atoms; packed two-wide FP32 arithmetic).
- * Without autotuning, batches of at least 1216 atoms take variant 2 and smaller ones variant 0
+ * lanes per unit of pairs (resident warps walking the atoms; packed two-wide FP32 arithmetic;
+ * the adjoint's 4 walks all units of an atom as one flattened pair range), and for the
+ * adjoint only 5 = the compensated kernel walking each atom's pairs in diagonal order
+ * (k, k + d mod n), whose rounds of min(32, n - 1) pairs touch distinct entries on each side,
+ * so the per-entry gradients are summed without atomics in a fixed order (bit-reproducible).
+ * Without autotuning, batches of at least 1216 atoms take variant 2 (adjoint: 5) and smaller ones variant 0
  * (several warps per atom).  knob "mlp_fp32" (PANNA_MLP_FP32 networks): a bit mask of the first layer's
  * products (descriptor width to first hidden width, almost all of the networks'
  * arithmetic) that run on the tensor cores with operands split into TF32 parts, the rest
@@ -236,8 +240,9 @@ panna_status panna_set_tuning(panna_ctx* ctx, const char* knob, int32_t value);
 
 /* The kernel variant that knob "descriptor", "adjoint" or "jvp" ran with in the last compute
  * call that used it (tuned or forced): 0 blocked, 1 flattened, 2 / 3 / 4 compensated with 32 / 16
- * / 8 lanes per (species block, theta chunk, R chunk) unit; -1 before any such call or for an
- * unknown knob. */
+ * / 8 lanes per (species block, theta chunk, R chunk) unit (adjoint 4: flattened units), 5
+ * (adjoint only) compensated in diagonal pair order; -1 before any such call or for an unknown
+ * knob. */
 int32_t panna_tuning_choice(const panna_ctx* ctx, const char* knob);
 
 /*

@@ -64,7 +64,9 @@ struct Arena {
     }
 };
 
-constexpr int kNumVariants = 5;   // descriptor-family kernel variants the tuner measures
+constexpr int kNumVariants = 6;   // most variants of one descriptor-family kernel
+// variants per kernel: descriptor and JVP 0..4, adjoint 0..5
+constexpr int kKindVariants[3] = {5, 6, 5};
 const char* kStages[] = {"neighbors", "descriptor", "mlp", "adjoint", "forces", "jvp", "mlp_grad", "loss"};
 constexpr int kNumStages = 8;
 
@@ -360,7 +362,9 @@ ParamRanges frozen_ranges(const panna_ctx* c)
 }
 
 // Kernel variants of the descriptor-family kernels for this problem signature (0 blocked,
-// 1 flattened, 2 / 3 / 4 compensated with 32 / 16 / 8 lanes per unit): measured once per kernel
+// 1 flattened, 2 / 3 / 4 compensated with 32 / 16 / 8 lanes per unit; the adjoint's 4 is the
+// flattened compensated walk and its 5 the diagonal-order walk without shared-memory atomics):
+// measured once per kernel
 // (each variant launched once to warm up, then timed with CUDA events on the caller's stream),
 // then cached.  Asynchronous calls never measure (they may be under stream capture) and use
 // the cached or default choice.
@@ -387,12 +391,13 @@ int tuned_variant_(panna_ctx* c, const panna_system* sys, int prec, int kind, cu
         if (q.N == sys->n_atoms && q.C == sys->n_cfg && q.cap == c->cap && q.prec == prec) t = &q;
     }
     if (t && t->variant[kind] >= 0) return t->variant[kind];
-    const int fallback = sys->n_atoms < kSplitAtoms ? 0 : 2;
+    const int fallback = sys->n_atoms < kSplitAtoms ? 0 : (kind == KV_ADJ ? 5 : 2);
     if (!c->autotune || c->async || sys->n_atoms == 0) return fallback;
     float ms[kNumVariants] = {};
-    for (int v = 0; v < kNumVariants; ++v) launch(v);   // first launches load and configure the kernels
+    const int nv = kKindVariants[kind];
+    for (int v = 0; v < nv; ++v) launch(v);   // first launches load and configure the kernels
     int best = 0;
-    for (int v = 0; v < kNumVariants; ++v) {
+    for (int v = 0; v < nv; ++v) {
         cudaEventRecord(c->tev[0], s);
         launch(v);
         cudaEventRecord(c->tev[1], s);
@@ -756,7 +761,7 @@ panna_status panna_set_tuning(panna_ctx* c, const char* knob, int32_t value)
     }
     const char* kinds[3] = {"descriptor", "adjoint", "jvp"};
     for (int k = 0; k < 3; ++k)
-        if (strcmp(knob, kinds[k]) == 0 && value >= -1 && value < kNumVariants) {
+        if (strcmp(knob, kinds[k]) == 0 && value >= -1 && value < kKindVariants[k]) {
             c->force_variant[k] = value;
             return PANNA_OK;
         }
