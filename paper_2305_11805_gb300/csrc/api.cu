@@ -167,6 +167,8 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, 
     w.atom_cfg = a.take<int32_t>(N);
     w.pos_hi = a.take<float4>(N);
     w.pos_lo = a.take<float4>(N);
+    w.pos_hi_s = a.take<float4>(N);
+    w.pos_lo_s = a.take<float4>(N);
     w.wrap = a.take<int32_t>(3 * N);
     int64_t mx = w.cap_cells + 1 > N + 1 ? w.cap_cells + 1 : N + 1;
     w.scan_tmp = a.take<int64_t>(scan_scratch_elems(mx));

@@ -101,6 +101,8 @@ struct Work {
     int32_t* atom_cfg;           // [N]
     float4* pos_hi;              // [N] folded position, hi part
     float4* pos_lo;              // [N] lo part
+    float4* pos_hi_s;            // [N] pos_hi in cell order (slot t holds atom cell_atoms[t])
+    float4* pos_lo_s;            // [N] pos_lo in cell order
     int32_t* wrap;               // [N*3] integer lattice offset added by folding
     int64_t* scan_tmp;           // scan scratch
     // neighbours

@@ -317,7 +317,12 @@ __global__ void k_scatter(int64_t N, const int32_t* __restrict__ atom_cfg, const
     cell_atoms[cell_start[gc] + k] = (int32_t)i;
 }
 
-__global__ void k_sort_cells(int64_t ncells, const int64_t* __restrict__ cell_start, int32_t* __restrict__ cell_atoms)
+// atoms of each cell sorted by index; with pos_hi_s / pos_lo_s, the folded positions copied in
+// that cell order (the candidate loop of the search then reads a candidate's position by its
+// slot, not through its atom index)
+__global__ void k_sort_cells(int64_t ncells, const int64_t* __restrict__ cell_start, int32_t* __restrict__ cell_atoms,
+                             const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo,
+                             float4* __restrict__ pos_hi_s, float4* __restrict__ pos_lo_s)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
@@ -327,6 +332,13 @@ __global__ void k_sort_cells(int64_t ncells, const int64_t* __restrict__ cell_st
         int64_t q = k - 1;
         while (q >= b && cell_atoms[q] > v) { cell_atoms[q + 1] = cell_atoms[q]; --q; }
         cell_atoms[q + 1] = v;
+    }
+    if (pos_hi_s) {
+        for (int64_t k = b; k < e; ++k) {
+            const int32_t j = cell_atoms[k];
+            pos_hi_s[k] = pos_hi[j];
+            pos_lo_s[k] = pos_lo[j];
+        }
     }
 }
 
@@ -385,7 +397,8 @@ __global__ void __launch_bounds__(kNbWarps * 32)
 k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__ geom,
             const int32_t* __restrict__ atom_cfg, const int32_t* __restrict__ atom_cell,
             const int64_t* __restrict__ cell_start, const int32_t* __restrict__ cell_atoms,
-            const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo, int cap,
+            const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo,
+            const float4* __restrict__ pos_hi_s, const float4* __restrict__ pos_lo_s, int cap,
             const uint8_t* __restrict__ ghost, int32_t* __restrict__ nb_count, float4* __restrict__ nb_vec,
             int2* __restrict__ nb_idx, DevStatus* st)
 {
@@ -393,8 +406,12 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* svec = reinterpret_cast<float4*>(smem_raw) + (size_t)warp * cap;
     int2* sidx = reinterpret_cast<int2*>(reinterpret_cast<float4*>(smem_raw) + (size_t)kNbWarps * cap) + (size_t)warp * cap;
-    const int64_t i = (int64_t)blockIdx.x * kNbWarps + warp;
-    if (i >= N) return;
+    // warps take the atoms in cell order (cell_atoms is a permutation of the atoms): the warps
+    // of a CTA scan overlapping windows of cells, so candidate positions come from L1
+    const int64_t gw = (int64_t)blockIdx.x * kNbWarps + warp;
+    if (gw >= N) return;
+    const int64_t i = cell_atoms[gw];
+    if (i < 0 || i >= N) return;   // not reached: every atom is binned into exactly one cell
     if (ghost && ghost[i]) {          // a ghost is a neighbour only, never a centre
         if (lane == 0) nb_count[i] = 0;
         return;
@@ -481,8 +498,9 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
             float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
             int j = -1, spj = 0;
             if (q < total) {
-                j = cell_atoms[beg_s + (q - pre_s)];
-                const float4 xjh = pos_hi[j];
+                const int64_t slot = beg_s + (q - pre_s);
+                j = cell_atoms[slot];
+                const float4 xjh = pos_hi_s[slot];
                 spj = __float_as_int(xjh.w);
                 const float fx = (xjh.x + cs.h0) - xih.x;
                 const float fy = (xjh.y + cs.h1) - xih.y;
@@ -490,7 +508,7 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
                 const float f2 = fx * fx + fy * fy + fz * fz;
                 const bool self_image = (tc & 0xffffff) == pack_meta(0, 0, 0, 0);
                 if (f2 < band2 && !(self_image && j == (int)i)) {
-                    const float4 xjl = pos_lo[j];
+                    const float4 xjl = pos_lo_s[slot];
                     dx = dd_rel(xjh.x, xjl.x, cs.h0, cs.l0, xih.x, xil.x);
                     dy = dd_rel(xjh.y, xjl.y, cs.h1, cs.l1, xih.y, xil.y);
                     dz = dd_rel(xjh.z, xjl.z, cs.h2, cs.l2, xih.z, xil.z);
@@ -713,7 +731,8 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
     e = exclusive_scan_i64(w.cell_count, w.cell_start, w.cap_cells, w.scan_tmp, s, launches);
     if (e != cudaSuccess) return e;
     k_scatter<<<nbA, 256, 0, s>>>(N, w.atom_cfg, w.atom_cell, w.geom, w.cell_start, w.cell_fill, w.cell_atoms);
-    k_sort_cells<<<(unsigned)((w.cap_cells + 255) / 256), 256, 0, s>>>(w.cap_cells, w.cell_start, w.cell_atoms);
+    k_sort_cells<<<(unsigned)((w.cap_cells + 255) / 256), 256, 0, s>>>(w.cap_cells, w.cell_start, w.cell_atoms,
+                                                                        w.pos_hi, w.pos_lo, w.pos_hi_s, w.pos_lo_s);
     *launches += 2;
     size_t smem = (size_t)kNbWarps * w.cap * (sizeof(float4) + sizeof(int2));
     e = cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -721,7 +740,8 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
     unsigned nbW = (unsigned)((N + kNbWarps - 1) / kNbWarps);
     if (nbW == 0) nbW = 1;
     k_neighbors<<<nbW, kNbWarps * 32, smem, s>>>(N, d.S, d.rc_d, d.rc, w.geom, w.atom_cfg, w.atom_cell,
-                                                 w.cell_start, w.cell_atoms, w.pos_hi, w.pos_lo, w.cap,
+                                                 w.cell_start, w.cell_atoms, w.pos_hi, w.pos_lo, w.pos_hi_s,
+                                                 w.pos_lo_s, w.cap,
                                                  w.sys->ghost, w.nb_count, w.nb_vec, w.nb_idx, w.status);
     ++*launches;
     return cudaGetLastError();
@@ -744,27 +764,57 @@ __global__ void k_species_count(int64_t N, int S, const float4* __restrict__ pos
     if (threadIdx.x < S) blk_counts[(size_t)blockIdx.x * S + threadIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void k_species_offsets(int64_t nblk, int S, int32_t* __restrict__ blk_counts, int32_t* __restrict__ seg_off)
+constexpr int kOffThreads = 1024;
+
+// Offsets of every (block, species) count: per species an exclusive scan over the blocks (one
+// CTA; each thread walks a contiguous run of blocks, a block-wide scan joins the runs), shifted
+// by the totals of the species before it; seg_off[s] = first row of species s.
+__global__ void __launch_bounds__(kOffThreads)
+k_species_offsets(int64_t nblk, int S, int32_t* __restrict__ blk_counts, int32_t* __restrict__ seg_off)
 {
-    __shared__ int tot[kMaxSpecies];
-    const int s = threadIdx.x;
-    if (s < S) {
-        int run = 0;
-        for (int64_t b = 0; b < nblk; ++b) {
-            int v = blk_counts[b * S + s];
+    __shared__ int wsum[kOffThreads / 32];
+    __shared__ int s_base;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int64_t per = (nblk + kOffThreads - 1) / kOffThreads;
+    const int64_t b0 = min(nblk, (int64_t)t * per), b1 = min(nblk, b0 + per);
+    if (t == 0) s_base = 0;
+    __syncthreads();
+    for (int s = 0; s < S; ++s) {
+        int sum = 0;
+        for (int64_t b = b0; b < b1; ++b) sum += blk_counts[b * S + s];
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int v = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        const int base = s_base;
+        int run = base + (wid > 0 ? wsum[wid - 1] : 0) + incl - sum;
+        for (int64_t b = b0; b < b1; ++b) {
+            const int v = blk_counts[b * S + s];
             blk_counts[b * S + s] = run;
             run += v;
         }
-        tot[s] = run;
+        __syncthreads();   // base and the warp sums are read
+        if (t == 0) {
+            seg_off[s] = base;
+            s_base = base + wsum[kOffThreads / 32 - 1];
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    if (s < S) {
-        int base = 0;
-        for (int k = 0; k < s; ++k) base += tot[k];
-        for (int64_t b = 0; b < nblk; ++b) blk_counts[b * S + s] += base;
-        seg_off[s] = base;
-        if (s == S - 1) seg_off[S] = base + tot[s];
-    }
+    if (t == 0) seg_off[S] = s_base;
 }
 
 __global__ void k_species_rank(int64_t N, int S, const float4* __restrict__ pos_hi, const uint8_t* __restrict__ ghost,
@@ -798,7 +848,7 @@ cudaError_t species_order(Work& w, int S, cudaStream_t s, int* launches)
     if (nblk == 0) nblk = 1;
     const uint8_t* ghost = w.sys->ghost;
     k_species_count<<<(unsigned)nblk, kSpBlock, 0, s>>>(w.N, S, w.pos_hi, ghost, w.blk_counts);
-    k_species_offsets<<<1, 32, 0, s>>>(nblk, S, w.blk_counts, w.seg_off);
+    k_species_offsets<<<1, kOffThreads, 0, s>>>(nblk, S, w.blk_counts, w.seg_off);
     k_species_rank<<<(unsigned)nblk, kSpBlock, 0, s>>>(w.N, S, w.pos_hi, ghost, w.blk_counts, w.row_of_atom,
                                                       w.atom_of_row);
     *launches += 3;

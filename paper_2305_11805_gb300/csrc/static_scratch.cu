@@ -61,6 +61,8 @@ size_t carve_static(char* base, int64_t N, int64_t C, int cap, Work& w)
     w.atom_cfg = a.take<int32_t>(N);
     w.pos_hi = a.take<float4>(N);
     w.pos_lo = a.take<float4>(N);
+    w.pos_hi_s = a.take<float4>(N);
+    w.pos_lo_s = a.take<float4>(N);
     w.wrap = a.take<int32_t>(3 * N);
     w.scan_tmp = a.take<int64_t>(scan_scratch_elems(w.cap_cells + 1 > N + 1 ? w.cap_cells + 1 : N + 1));
     w.nb_count = a.take<int32_t>(N);
