@@ -197,9 +197,11 @@ panna_status panna_set_async(panna_ctx* ctx, int32_t async);
 
 /*
  * Arithmetic of the angular descriptor terms in kernel variants 0 and 1 (descriptor, adjoint,
- * JVP; the compensated variants 2..4 always evaluate the angle from the cross product of the
- * FP32 relative vectors, t_m = 1 - y_m from the half angles and y^zeta from a series of
- * log(1 - t), which is about as accurate as the extended mode below at plain-FP32 cost):
+ * JVP; the compensated variants 2..5 always evaluate the angle from the FP32 relative vectors,
+ * t_m = 1 - y_m from the half angles and y^zeta from a series of log(1 - t): far more accurate
+ * than plain FP32 at plain-FP32 cost, but the angle itself stays a single float, which the
+ * zeta-th power turns into ~1e-6 relative per term, so with FP32 networks the autotuner gives
+ * the descriptor only variants 0 and 1, in the extended mode below):
  *   0 = automatic (default): extended precision for the descriptor and the adjoint with FP32
  *       networks (force tolerance 1e-5 of RMS), plain FP32 with the BF16 modes (their
  *       tolerance is 1e-2) and for the JVP of the weight gradient (tolerance 1e-4);
@@ -224,7 +226,9 @@ panna_status panna_set_angular_precision(panna_ctx* ctx, int32_t mode);
  * adjoint only 5 = the compensated kernel walking each atom's pairs in diagonal order
  * (k, k + d mod n), whose rounds of min(32, n - 1) pairs touch distinct entries on each side,
  * so the per-entry gradients are summed without atomics in a fixed order (bit-reproducible).
- * Without autotuning, batches of at least 1216 atoms take variant 2 (adjoint: 5) and smaller ones variant 0
+ * With FP32 networks (extended angular terms) the descriptor's candidates are variants 0 and 1
+ * only.  Without autotuning, batches of at least 1216 atoms take variant 2 (adjoint: 5; the
+ * descriptor with FP32 networks: 0) and smaller ones variant 0
  * (several warps per atom).  knob "mlp_fp32" (PANNA_MLP_FP32 networks): a bit mask of the first layer's
  * products (descriptor width to first hidden width, almost all of the networks'
  * arithmetic) that run on the tensor cores with operands split into TF32 parts, the rest

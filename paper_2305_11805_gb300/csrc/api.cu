@@ -93,7 +93,8 @@ struct panna_ctx {
     QeqDev qeq{};                     // charge-equilibration constants (3-output networks)
     bool qeq_set = false;
     // autotuner: kernel variant per problem signature, measured on the first call
-    struct Tuned { int64_t N, C; int cap, prec; int variant[3]; };   // -1 = not measured yet
+    // per problem signature (atoms, configurations, capacity, precision, extended angular terms)
+    struct Tuned { int64_t N, C; int cap, prec, ext; int variant[3]; };   // -1 = not measured yet
     Tuned tuned[16];
     int n_tuned = 0;
     cudaEvent_t tev[3] = {};
@@ -175,6 +176,8 @@ void carve(panna_ctx* c, Arena& a, int64_t N, int64_t C, bool train, bool bf16, 
     w.nb_count = a.take<int32_t>(N);
     w.nb_vec = a.take<float4>((size_t)N * cap);
     w.nb_idx = a.take<int2>((size_t)N * cap);
+    // low parts of the neighbour vectors, for the float-pair angular terms of FP32 networks
+    w.nb_vlo = bf16 ? nullptr : a.take<float4>((size_t)N * cap);
     w.row_of_atom = a.take<int32_t>(N);
     w.atom_of_row = a.take<int32_t>(N);
     w.seg_off = a.take<int32_t>(S + 1);
@@ -373,30 +376,37 @@ ParamRanges frozen_ranges(const panna_ctx* c)
 enum { KV_DESC = 0, KV_ADJ = 1, KV_JVP = 2 };
 
 template <class Launch>
-int tuned_variant_(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch);
+int tuned_variant_(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch, bool ext);
 
+// ext (descriptor with FP32 networks, force tolerance 1e-5 of RMS): only the kernels that carry
+// the angular terms as float pairs (variants 0 and 1) are candidates.  The compensated FP32
+// kernels keep the angle in single floats, whose rounding (about 6e-8 rad) the zeta-th power
+// turns into ~1e-6 relative per term; on the 1024 molecules that put one atom's force at
+// 0.95-1.16e-5 of RMS against 4.3e-6 with the float pairs.
 template <class Launch>
-int tuned_variant(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch)
+int tuned_variant(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch,
+                  bool ext = false)
 {
-    const int v = tuned_variant_(c, sys, prec, kind, s, launch);
+    const int v = tuned_variant_(c, sys, prec, kind, s, launch, ext && kind == KV_DESC);
     c->last_variant[kind] = v;
     return v;
 }
 
 template <class Launch>
-int tuned_variant_(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch)
+int tuned_variant_(panna_ctx* c, const panna_system* sys, int prec, int kind, cudaStream_t s, Launch launch, bool ext)
 {
     if (c->force_variant[kind] >= 0) return c->force_variant[kind];
     panna_ctx::Tuned* t = nullptr;
     for (int k = 0; k < c->n_tuned; ++k) {
         panna_ctx::Tuned& q = c->tuned[k];
-        if (q.N == sys->n_atoms && q.C == sys->n_cfg && q.cap == c->cap && q.prec == prec) t = &q;
+        if (q.N == sys->n_atoms && q.C == sys->n_cfg && q.cap == c->cap && q.prec == prec && q.ext == (int)ext)
+            t = &q;
     }
     if (t && t->variant[kind] >= 0) return t->variant[kind];
-    const int fallback = sys->n_atoms < kSplitAtoms ? 0 : (kind == KV_ADJ ? 5 : 2);
+    const int fallback = (sys->n_atoms < kSplitAtoms || ext) ? 0 : (kind == KV_ADJ ? 5 : 2);
     if (!c->autotune || c->async || sys->n_atoms == 0) return fallback;
     float ms[kNumVariants] = {};
-    const int nv = kKindVariants[kind];
+    const int nv = ext ? 2 : kKindVariants[kind];
     for (int v = 0; v < nv; ++v) launch(v);   // first launches load and configure the kernels
     int best = 0;
     for (int v = 0; v < nv; ++v) {
@@ -409,7 +419,7 @@ int tuned_variant_(panna_ctx* c, const panna_system* sys, int prec, int kind, cu
     }
     if (!t) {
         t = &c->tuned[c->n_tuned < 16 ? c->n_tuned++ : 15];
-        *t = panna_ctx::Tuned{sys->n_atoms, sys->n_cfg, c->cap, prec, {-1, -1, -1}};
+        *t = panna_ctx::Tuned{sys->n_atoms, sys->n_cfg, c->cap, prec, (int)ext, {-1, -1, -1}};
     }
     t->variant[kind] = best;
     return best;
@@ -423,6 +433,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
     // FP32 networks get the extended-precision angular terms (force tolerance 1e-5 of RMS);
     // BF16 networks (tolerance 1e-2) the plain FP32 form
     const bool acc = c->ang_mode == 1 || (c->ang_mode == 0 && rq.prec == PANNA_MLP_FP32);
+    if (!acc) L.w.nb_vlo = nullptr;   // the plain and compensated kernels read no low parts
     for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
     c->n_marked = 0;
     CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
@@ -456,7 +467,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         int dummy = 0;
         const int v = tuned_variant(c, sys, rq.prec, KV_DESC, s, [&](int vv) {
             launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &dummy, vv);
-        });
+        }, acc);
         const bool tcp = rq.prec == PANNA_MLP_BF16 || rq.prec == PANNA_MLP_BF16_FAST;
         __nv_bfloat16 *gh = nullptr, *gl = nullptr;
         if (tcp) tc_g16(c->plan, N, rq.prec == PANNA_MLP_BF16, L.tc_ws, &gh, &gl);
@@ -589,6 +600,7 @@ panna_status md_build(panna_ctx* c, const panna_system* sys, Layout& L, Work& wc
     wc.nb_count = L.cand_count;
     wc.nb_vec = L.cand_vec;
     wc.nb_idx = L.cand_idx;
+    wc.nb_vlo = nullptr;   // candidates keep no low parts (the refresh forms them at each step)
     wc.cap = c->cap_c;
     DescDev dc = c->d;
     dc.rc_d = c->d.rc_d + skin;
@@ -927,6 +939,7 @@ panna_status panna_neighbors(panna_ctx* c, const panna_system* sys, int64_t cap_
     for (int attempt = 0; attempt < 2; ++attempt) {
         Layout L;
         ST(prepare(c, sys, false, false, L, s));
+        L.w.nb_vlo = nullptr;   // the export needs no low parts
         c->last_launches = 0;
         CU(cudaMemsetAsync(L.w.status, 0, sizeof(DevStatus), s));
         CU(build_neighbors(L.w, c->d, s, &c->last_launches));
@@ -1032,6 +1045,7 @@ panna_status panna_qeq_energy_forces(panna_ctx* c, const panna_system* sys, cons
     for (int attempt = 0; attempt < 2; ++attempt) {
         Layout L;
         ST(prepare(c, sys, false, false, L, s));
+        if (!acc) L.w.nb_vlo = nullptr;
         int& nl = c->last_launches;
         nl = 0;
         for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
@@ -1045,7 +1059,7 @@ panna_status panna_qeq_energy_forces(panna_ctx* c, const panna_system* sys, cons
         int dummy = 0;
         const int vd = tuned_variant(c, sys, PANNA_MLP_FP32, KV_DESC, s, [&](int vv) {
             launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &dummy, vv);
-        });
+        }, acc);
         CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl, vd));
         stage_mark(c, 2, s);
         CU(mlp_forward(c->plan, L.mb, theta, N, s, &nl));
@@ -1103,6 +1117,7 @@ panna_status panna_qeq_loss_grad(panna_ctx* c, const panna_system* sys, const fl
     for (int attempt = 0; attempt < 2; ++attempt) {
         Layout L;
         ST(prepare(c, sys, true, false, L, s));
+        if (!acc) L.w.nb_vlo = nullptr;
         int& nl = c->last_launches;
         nl = 0;
         for (int k = 0; k < kNumStages; ++k) c->stage_seen[k] = false;
@@ -1118,7 +1133,7 @@ panna_status panna_qeq_loss_grad(panna_ctx* c, const panna_system* sys, const fl
         int dummy = 0;
         const int vd = tuned_variant(c, sys, PANNA_MLP_FP32, KV_DESC, s, [&](int vv) {
             launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &dummy, vv);
-        });
+        }, acc);
         CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl, vd));
         stage_mark(c, 2, s);
         CU(mlp_forward(c->plan, L.mb, theta, N, s, &nl));
@@ -1277,7 +1292,7 @@ panna_status panna_store_build(panna_ctx* c, const panna_system* sys, const pann
     int dummy = 0;
     const int variant = tuned_variant(c, sys, PANNA_MLP_FP32, KV_DESC, s, [&](int vv) {
         launch_descriptor(L.w, c->d, v.G, L.w.row_of_atom, acc, s, &dummy, vv);
-    });
+    }, acc);
     CU(launch_descriptor(L.w, c->d, v.G, L.w.row_of_atom, acc, s, &nl, variant));
     const int64_t N = sys->n_atoms;
     CU(cudaMemcpyAsync(v.row_of_atom, L.w.row_of_atom, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s));

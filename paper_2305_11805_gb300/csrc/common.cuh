@@ -108,6 +108,9 @@ struct Work {
     // neighbours
     int32_t* nb_count;           // [N]
     float4* nb_vec;              // [N*cap] (dx, dy, dz, r)
+    // [N*cap] low parts (dx - (float)dx, ...) of the relative vectors formed in double-float, or
+    // null: written and read only for the float-pair angular terms (FP32 networks)
+    float4* nb_vlo;
     int2* nb_idx;                // [N*cap] (j, meta)
     // species order
     int32_t* row_of_atom;        // [N]

@@ -54,6 +54,8 @@ struct TcCfg {
     static constexpr uint32_t kTileB = kMaxBN * kTcBK * 2;
     static constexpr uint32_t kStageB = kParts * kTileB;
     static constexpr size_t kSmem = 1024 + kStages * (kStageA + kStageB) + 256;
+    // the persistent kernel adds a 2 KB staging tile per epilogue warp for its FP32 outputs
+    static constexpr size_t kSmemP = kSmem + 2048 * 8;
 };
 
 enum { TC_FWD = 1, TC_BWD_MID = 2, TC_BWD_OUT = 3, TC_FWD32 = 4, TC_TAN32 = 5, TC_WGRAD = 6 };
@@ -888,6 +890,8 @@ k_tc_gemm_p(const __grid_constant__ TcMaps tm, TcArgs a, int n_nt)
     uint64_t* acce = accf + 2;                           // [2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    // FP32 output staging, 2 KB per epilogue warp, past the barriers (kSmemP - kSmem bytes)
+    float* stg = reinterpret_cast<float*>(sB + kStages * Cfg::kStageB + 256);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_items = a.tile_start[a.S] * n_nt;
@@ -980,49 +984,105 @@ k_tc_gemm_p(const __grid_constant__ TcMaps tm, TcArgs a, int n_nt)
             const ItemPos ip = tc_item(a, item, n_nt);
             if (!ip.valid) continue;
             const int b = j & 1;
-            if (!mbar_wait(accf + b, (uint32_t)(j >> 1) & 1u, abort_flag)) { *abort_flag = 1; break; }
-            tc_fence_after();
             const int r = ip.row0 + q * 32 + lane;
             const bool row_ok = r < ip.rend;
             const int s = ip.s, Ns = a.N[s];
+            // BWD_MID: the pre-activations of the next 16 columns are loaded one chunk ahead (the
+            // first before the wait for the MMAs), so their latency overlaps the TMEM wait and the
+            // previous chunk's arithmetic and stores
+            float zn[16];
+            auto load_z = [&](int c) {
+                const int n = ip.n0 + c;
+                if (EPI != TC_BWD_MID || !row_ok || c >= a.BN || n >= Ns) return;
+                const float* z = a.Zin + (size_t)r * a.ldZ + n;
+                if (n + 16 <= Ns && (reinterpret_cast<uintptr_t>(z) & 15) == 0) {
+#pragma unroll
+                    for (int k = 0; k < 16; k += 4) {
+                        const float4 t4 = *reinterpret_cast<const float4*>(z + k);
+                        zn[k] = t4.x; zn[k + 1] = t4.y; zn[k + 2] = t4.z; zn[k + 3] = t4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) zn[k] = (n + k < Ns) ? z[k] : 0.f;
+                }
+            };
+            load_z(half * 16);
+            if (!mbar_wait(accf + b, (uint32_t)(j >> 1) & 1u, abort_flag)) { *abort_flag = 1; break; }
+            tc_fence_after();
             for (int c0 = half * 16; c0 < a.BN; c0 += 32) {
                 float v[16];
                 tc_ld16(tmem + (uint32_t)b * kAcc + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
                 const int n = ip.n0 + c0;
-                if (!row_ok || n >= Ns) continue;
+                if (n >= Ns) continue;   // the same for the whole warp
                 const bool whole = n + 16 <= Ns;
+                float zv[16];
+                if (EPI == TC_BWD_MID) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) zv[k] = zn[k];
+                    load_z(c0 + 32);
+                }
                 float o1[16], o2[16];
                 if (EPI == TC_FWD) {
                     const float* bias = a.bias + s * a.n_pad + n;
+                    float bv[16];
+                    if ((reinterpret_cast<uintptr_t>(bias) & 15) == 0) {
+#pragma unroll
+                        for (int k = 0; k < 16; k += 4) {
+                            const float4 t4 = *reinterpret_cast<const float4*>(bias + k);
+                            bv[k] = t4.x; bv[k + 1] = t4.y; bv[k + 2] = t4.z; bv[k + 3] = t4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) bv[k] = bias[k];
+                    }
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        o1[k] = v[k] + bias[k];
+                        o1[k] = v[k] + bv[k];
                         o2[k] = act_f(a.act[s], o1[k]);
                     }
                 } else if (EPI == TC_BWD_MID) {
-                    const float* z = a.Zin + (size_t)r * a.ldZ + n;
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) o2[k] = (whole || n + k < Ns) ? v[k] * act_d1(a.act[s], z[k]) : 0.f;
+                    for (int k = 0; k < 16; ++k) o2[k] = (whole || n + k < Ns) ? v[k] * act_d1(a.act[s], zv[k]) : 0.f;
                 } else {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) o1[k] = v[k];
                 }
                 if (EPI == TC_FWD || EPI == TC_BWD_OUT) {
-                    float* o = a.outF + (size_t)r * a.ldF + n;
-                    if (whole && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+                    const bool aligned = (a.ldF & 3) == 0 &&
+                                         (reinterpret_cast<uintptr_t>(a.outF + (size_t)ip.row0 * a.ldF + n) & 15) == 0;
+                    if (whole && aligned) {
+                        // through the warp's staging tile: each lane writes its row's 16 values
+                        // (16-byte pieces swizzled by row, conflict-free), then the warp stores
+                        // 8 rows x 64 contiguous bytes per instruction instead of 32 rows x 16
+                        float* st = stg + ew * 512;
+                        const int sw = (lane >> 1) & 3;
 #pragma unroll
-                        for (int k = 0; k < 16; k += 4)
-                            *reinterpret_cast<float4*>(o + k) = make_float4(o1[k], o1[k + 1], o1[k + 2], o1[k + 3]);
-                    } else {
+                        for (int k = 0; k < 4; ++k)
+                            *reinterpret_cast<float4*>(st + lane * 16 + 4 * (k ^ sw)) =
+                                make_float4(o1[4 * k], o1[4 * k + 1], o1[4 * k + 2], o1[4 * k + 3]);
+                        __syncwarp();
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int row = i * 8 + (lane >> 2), pc = lane & 3;
+                            const float4 val = *reinterpret_cast<const float4*>(st + row * 16 + 4 * (pc ^ ((row >> 1) & 3)));
+                            const int rr = ip.row0 + q * 32 + row;
+                            if (rr < ip.rend)
+                                *reinterpret_cast<float4*>(a.outF + (size_t)rr * a.ldF + n + 4 * pc) = val;
+                        }
+                        __syncwarp();
+                    } else if (row_ok) {
+                        float* o = a.outF + (size_t)r * a.ldF + n;
 #pragma unroll
                         for (int k = 0; k < 16; ++k)
                             if (n + k < Ns) o[k] = o1[k];
                     }
                 }
                 if (EPI == TC_FWD || EPI == TC_BWD_MID) {
-                    __nv_bfloat16* oh = a.outH + (size_t)r * a.ldH + n;
-                    __nv_bfloat16* ol = PARTS >= 2 ? a.outL + (size_t)r * a.ldH + n : nullptr;
-                    if (whole && (reinterpret_cast<uintptr_t>(oh) & 15) == 0) {
+                    const bool aligned = (a.ldH & 7) == 0 &&
+                                         (reinterpret_cast<uintptr_t>(a.outH + (size_t)ip.row0 * a.ldH + n) & 15) == 0 &&
+                                         (PARTS < 2 ||
+                                          (reinterpret_cast<uintptr_t>(a.outL + (size_t)ip.row0 * a.ldH + n) & 15) == 0);
+                    if (whole && aligned) {
                         uint32_t hw[8], lw[8];
 #pragma unroll
                         for (int k = 0; k < 16; k += 2) {
@@ -1032,15 +1092,32 @@ k_tc_gemm_p(const __grid_constant__ TcMaps tm, TcArgs a, int n_nt)
                             hw[k / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
                             lw[k / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
                         }
-                        uint4* dh = reinterpret_cast<uint4*>(oh);
-                        dh[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        dh[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+                        // through the staging tile: hi rows then lo rows, 32 B per row, the two
+                        // 16-byte pieces swapped on every other group of four rows (conflict-free);
+                        // the warp then stores 16 rows x 32 contiguous bytes per instruction
+                        uint4* st = reinterpret_cast<uint4*>(stg + ew * 512);
+                        const int sw = (lane >> 2) & 1;
+                        st[lane * 2 + (0 ^ sw)] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        st[lane * 2 + (1 ^ sw)] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
                         if (PARTS >= 2) {
-                            uint4* dl = reinterpret_cast<uint4*>(ol);
-                            dl[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                            dl[1] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+                            st[64 + lane * 2 + (0 ^ sw)] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                            st[64 + lane * 2 + (1 ^ sw)] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
                         }
-                    } else {
+                        __syncwarp();
+#pragma unroll
+                        for (int part = 0; part < (PARTS >= 2 ? 2 : 1); ++part) {
+                            __nv_bfloat16* base = part ? a.outL : a.outH;
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) {
+                                const int row = i * 16 + (lane >> 1), pc = lane & 1;
+                                const uint4 val = st[part * 64 + row * 2 + (pc ^ ((row >> 2) & 1))];
+                                const int rr = ip.row0 + q * 32 + row;
+                                if (rr < ip.rend)
+                                    *reinterpret_cast<uint4*>(base + (size_t)rr * a.ldH + n + 8 * pc) = val;
+                            }
+                        }
+                        __syncwarp();
+                    } else if (row_ok) {
 #pragma unroll
                         for (int k = 0; k < 16; ++k)
                             if (n + k < Ns)
@@ -1086,7 +1163,7 @@ cudaError_t launch_tc_p(const TcMaps& m, const TcArgs& ta, int64_t N, int nmax, 
     const int n_nt = (nmax + ta.BN - 1) / ta.BN;
     const int64_t items = ((N + kTcBM - 1) / kTcBM + ta.S) * n_nt;
     const unsigned grid = (unsigned)std::min<int64_t>(items, n_sm);
-    const int smem = (int)TcCfg<PARTS>::kSmem;
+    const int smem = (int)TcCfg<PARTS>::kSmemP;
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_p<EPI, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_tc_gemm_p<EPI, PARTS><<<grid, kTcThreads, smem, s>>>(m, ta, n_nt);
@@ -1201,13 +1278,18 @@ cudaError_t mlp_bf16_energy_grad(const MlpPlan& p, const MlpBuffers& b, const fl
                                                                     t.Wb[l][0], t.Wb[l][1], nullptr, nullptr);
         *launches += 2;
     }
-    // padding columns of the BF16 operands meet zero weights, but must not hold NaN
-    for (int l = 1; l < p.L; ++l)
+    // padding columns of the BF16 operands meet zero weights, but must not hold NaN (the
+    // epilogues write the species' own columns only); layers without padding need no clearing
+    for (int l = 1; l < p.L; ++l) {
+        bool pad = false;
+        for (int q = 0; q < p.S; ++q) pad = pad || p.widths[q][l] != t.ldh[l];
+        if (!pad) continue;
         for (int q = 0; q < parts; ++q) {
             e = cudaMemsetAsync(t.A16[l][q], 0, (size_t)N * t.ldh[l] * 2, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(t.Zb16[l][q], 0, (size_t)N * t.ldh[l] * 2, s);
             if (e != cudaSuccess) return e;
         }
+    }
     if (!g16_ready) {
         k_to_bf16<<<(unsigned)((N * t.ldh[0] + 255) / 256), 256, 0, s>>>(N * t.ldh[0], b.G, t.G16[0], t.G16[1]);
         ++*launches;

@@ -353,14 +353,15 @@ __device__ __forceinline__ float two_sum(float a, float b, float& err)
     return s;
 }
 
-// (xj + S) - xi with each operand given as hi + lo, to about one FP32 rounding
-__device__ __forceinline__ float dd_rel(float xjh, float xjl, float sh, float sl, float xih, float xil)
+// (xj + S) - xi with each operand given as hi + lo, to about one FP32 rounding; lo receives
+// what the rounded result leaves of the double-float value (about 2^-46 of it)
+__device__ __forceinline__ float dd_rel(float xjh, float xjl, float sh, float sl, float xih, float xil, float& lo)
 {
     float e1, e2;
     float a = two_sum(xjh, sh, e1);
     float b = two_sum(a, -xih, e2);
     float tail = __fsub_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(xjl, sl)), xil);
-    return __fadd_rn(b, tail);
+    return two_sum(b, tail, lo);
 }
 
 constexpr int kNbWarps = 8;
@@ -400,12 +401,16 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
             const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo,
             const float4* __restrict__ pos_hi_s, const float4* __restrict__ pos_lo_s, int cap,
             const uint8_t* __restrict__ ghost, int32_t* __restrict__ nb_count, float4* __restrict__ nb_vec,
-            int2* __restrict__ nb_idx, DevStatus* st)
+            int2* __restrict__ nb_idx, float4* __restrict__ nb_vlo, DevStatus* st)
 {
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* svec = reinterpret_cast<float4*>(smem_raw) + (size_t)warp * cap;
     int2* sidx = reinterpret_cast<int2*>(reinterpret_cast<float4*>(smem_raw) + (size_t)kNbWarps * cap) + (size_t)warp * cap;
+    // low parts of the vectors (only with nb_vlo), after the index slots
+    float4* svlo = reinterpret_cast<float4*>(reinterpret_cast<int2*>(reinterpret_cast<float4*>(smem_raw) +
+                                                                     (size_t)kNbWarps * cap) + (size_t)kNbWarps * cap) +
+                   (size_t)warp * cap;
     // warps take the atoms in cell order (cell_atoms is a permutation of the atoms): the warps
     // of a CTA scan overlapping windows of cells, so candidate positions come from L1
     const int64_t gw = (int64_t)blockIdx.x * kNbWarps + warp;
@@ -495,7 +500,7 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
             cs.l1 = __shfl_sync(0xffffffffu, sh.l1, sl);
             cs.l2 = __shfl_sync(0xffffffffu, sh.l2, sl);
             bool in = false;
-            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
             int j = -1, spj = 0;
             if (q < total) {
                 const int64_t slot = beg_s + (q - pre_s);
@@ -509,9 +514,9 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
                 const bool self_image = (tc & 0xffffff) == pack_meta(0, 0, 0, 0);
                 if (f2 < band2 && !(self_image && j == (int)i)) {
                     const float4 xjl = pos_lo_s[slot];
-                    dx = dd_rel(xjh.x, xjl.x, cs.h0, cs.l0, xih.x, xil.x);
-                    dy = dd_rel(xjh.y, xjl.y, cs.h1, cs.l1, xih.y, xil.y);
-                    dz = dd_rel(xjh.z, xjl.z, cs.h2, cs.l2, xih.z, xil.z);
+                    dx = dd_rel(xjh.x, xjl.x, cs.h0, cs.l0, xih.x, xil.x, lx);
+                    dy = dd_rel(xjh.y, xjl.y, cs.h1, cs.l1, xih.y, xil.y, ly);
+                    dz = dd_rel(xjh.z, xjl.z, cs.h2, cs.l2, xih.z, xil.z, lz);
                     r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
                     if (fabsf(r2 - rc2) <= 2e-6f * rc2) {
                         in = retest_fp64(xjh, xjl, cs, xih, xil, rc2d);   // FP64 near the cutoff
@@ -527,6 +532,7 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
                 if (pos < cap) {
                     svec[pos] = make_float4(dx, dy, dz, sqrtf(r2));
                     sidx[pos] = make_int2(j, tc | (spj << 24));
+                    if (nb_vlo) svlo[pos] = make_float4(lx, ly, lz, 0.f);
                 }
             }
             count += __popc(mask);
@@ -541,7 +547,11 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
     __syncwarp();
     const size_t out = (size_t)i * cap;
     if (S == 1) {
-        for (int k = lane; k < n; k += 32) { nb_vec[out + k] = svec[k]; nb_idx[out + k] = sidx[k]; }
+        for (int k = lane; k < n; k += 32) {
+            nb_vec[out + k] = svec[k];
+            nb_idx[out + k] = sidx[k];
+            if (nb_vlo) nb_vlo[out + k] = svlo[k];
+        }
         return;
     }
     int w = 0;
@@ -554,6 +564,7 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
                 const int p = w + __popc(mask & lt);
                 nb_vec[out + p] = svec[k];
                 nb_idx[out + p] = sidx[k];
+                if (nb_vlo) nb_vlo[out + p] = svlo[k];
             }
             w += __popc(mask);
         }
@@ -589,7 +600,8 @@ __global__ void __launch_bounds__(kNbWarps * 32)
 k_refresh(int64_t N, double rc_d, float rc, const CfgGeom* __restrict__ geom, const int32_t* __restrict__ atom_cfg,
           const int32_t* __restrict__ cand_count, const int2* __restrict__ cand_idx, int cap_c,
           const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo, int cap,
-          int32_t* __restrict__ nb_count, float4* __restrict__ nb_vec, int2* __restrict__ nb_idx, DevStatus* st)
+          int32_t* __restrict__ nb_count, float4* __restrict__ nb_vec, int2* __restrict__ nb_idx,
+          float4* __restrict__ nb_vlo, DevStatus* st)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kNbWarps + warp;
@@ -605,7 +617,7 @@ k_refresh(int64_t N, double rc_d, float rc, const CfgGeom* __restrict__ geom, co
     for (int base = 0; base < nc; base += 32) {
         const int k = base + lane;
         bool in = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
         int2 e = make_int2(0, 0);
         if (k < nc) {
             e = cand_idx[cin + k];
@@ -621,9 +633,9 @@ k_refresh(int64_t N, double rc_d, float rc, const CfgGeom* __restrict__ geom, co
             const float fx = (xjh.x + cs.h0) - xih.x, fy = (xjh.y + cs.h1) - xih.y, fz = (xjh.z + cs.h2) - xih.z;
             if (fx * fx + fy * fy + fz * fz < band2) {
                 const float4 xjl = pos_lo[e.x];
-                dx = dd_rel(xjh.x, xjl.x, cs.h0, cs.l0, xih.x, xil.x);
-                dy = dd_rel(xjh.y, xjl.y, cs.h1, cs.l1, xih.y, xil.y);
-                dz = dd_rel(xjh.z, xjl.z, cs.h2, cs.l2, xih.z, xil.z);
+                dx = dd_rel(xjh.x, xjl.x, cs.h0, cs.l0, xih.x, xil.x, lx);
+                dy = dd_rel(xjh.y, xjl.y, cs.h1, cs.l1, xih.y, xil.y, ly);
+                dz = dd_rel(xjh.z, xjl.z, cs.h2, cs.l2, xih.z, xil.z, lz);
                 r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
                 if (fabsf(r2 - rc2) <= 2e-6f * rc2) in = retest_fp64(xjh, xjl, cs, xih, xil, rc2d);
                 else in = r2 < rc2;
@@ -636,6 +648,7 @@ k_refresh(int64_t N, double rc_d, float rc, const CfgGeom* __restrict__ geom, co
             if (p < cap) {
                 nb_vec[out + p] = make_float4(dx, dy, dz, sqrtf(r2));
                 nb_idx[out + p] = e;
+                if (nb_vlo) nb_vlo[out + p] = make_float4(lx, ly, lz, 0.f);
             }
         }
         count += __popc(mask);
@@ -655,7 +668,7 @@ cudaError_t refresh_neighbors(const Work& cand, Work& w, const DescDev& d, cudaS
                                                               w.pos_lo);
     k_refresh<<<(unsigned)((N + kNbWarps - 1) / kNbWarps), kNbWarps * 32, 0, s>>>(
         N, d.rc_d, d.rc, w.geom, w.atom_cfg, cand.nb_count, cand.nb_idx, cand.cap, w.pos_hi, w.pos_lo, w.cap,
-        w.nb_count, w.nb_vec, w.nb_idx, w.status);
+        w.nb_count, w.nb_vec, w.nb_idx, w.nb_vlo, w.status);
     *launches += 2;
     return cudaGetLastError();
 }
@@ -734,7 +747,7 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
     k_sort_cells<<<(unsigned)((w.cap_cells + 255) / 256), 256, 0, s>>>(w.cap_cells, w.cell_start, w.cell_atoms,
                                                                         w.pos_hi, w.pos_lo, w.pos_hi_s, w.pos_lo_s);
     *launches += 2;
-    size_t smem = (size_t)kNbWarps * w.cap * (sizeof(float4) + sizeof(int2));
+    size_t smem = (size_t)kNbWarps * w.cap * (sizeof(float4) + sizeof(int2) + (w.nb_vlo ? sizeof(float4) : 0));
     e = cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     unsigned nbW = (unsigned)((N + kNbWarps - 1) / kNbWarps);
@@ -742,7 +755,7 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
     k_neighbors<<<nbW, kNbWarps * 32, smem, s>>>(N, d.S, d.rc_d, d.rc, w.geom, w.atom_cfg, w.atom_cell,
                                                  w.cell_start, w.cell_atoms, w.pos_hi, w.pos_lo, w.pos_hi_s,
                                                  w.pos_lo_s, w.cap,
-                                                 w.sys->ghost, w.nb_count, w.nb_vec, w.nb_idx, w.status);
+                                                 w.sys->ghost, w.nb_count, w.nb_vec, w.nb_idx, w.nb_vlo, w.status);
     ++*launches;
     return cudaGetLastError();
 }

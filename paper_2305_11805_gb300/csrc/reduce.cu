@@ -63,17 +63,28 @@ k_cfg_partial(int64_t C, const int64_t* __restrict__ atom_off, int B, const int3
     }
 }
 
-__global__ void k_cfg_final(int64_t C, int B, const double* __restrict__ part, double* __restrict__ E_cfg,
-                            double* __restrict__ virial)
+// one warp per configuration: lane l sums the chunks l, l + 32, ... in order, then a fixed
+// butterfly joins the lanes (the same order on every call: energies are bit-reproducible)
+__global__ void __launch_bounds__(kCfgRedWarps * 32)
+k_cfg_final(int64_t C, int B, const double* __restrict__ part, double* __restrict__ E_cfg,
+            double* __restrict__ virial)
 {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * kCfgRedWarps + (threadIdx.x >> 5);
     if (c >= C) return;
     double v[kCfgVals];
+#pragma unroll
     for (int k = 0; k < kCfgVals; ++k) v[k] = 0.0;
-    for (int b = 0; b < B; ++b)
+    for (int b = lane; b < B; b += 32)
+#pragma unroll
         for (int k = 0; k < kCfgVals; ++k) v[k] += part[((size_t)c * B + b) * kCfgVals + k];
-    if (E_cfg) E_cfg[c] = v[0];
-    if (virial)
+#pragma unroll
+    for (int k = 0; k < kCfgVals; ++k)
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0 && E_cfg) E_cfg[c] = v[0];
+    if (lane == 0 && virial)
+#pragma unroll
         for (int k = 0; k < 9; ++k) virial[9 * c + k] = v[1 + k];
 }
 
@@ -89,7 +100,8 @@ cudaError_t launch_cfg_reduce(const Work& w, const float* E_rows, const float* v
     const int B = cfg_chunks(w.N, w.C);
     k_cfg_partial<<<(unsigned)((w.C * B + kCfgRedWarps - 1) / kCfgRedWarps), kCfgRedWarps * 32, 0, s>>>(
         w.C, w.sys->atom_off, B, w.row_of_atom, E_rows, vir_atom, E_atom, part);
-    k_cfg_final<<<(unsigned)((w.C + 127) / 128), 128, 0, s>>>(w.C, B, part, E_cfg, virial);
+    k_cfg_final<<<(unsigned)((w.C + kCfgRedWarps - 1) / kCfgRedWarps), kCfgRedWarps * 32, 0, s>>>(w.C, B, part,
+                                                                                                  E_cfg, virial);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -68,6 +68,7 @@ size_t carve_static(char* base, int64_t N, int64_t C, int cap, Work& w)
     w.nb_count = a.take<int32_t>(N);
     w.nb_vec = a.take<float4>((size_t)N * cap);
     w.nb_idx = a.take<int2>((size_t)N * cap);
+    w.nb_vlo = nullptr;
     w.row_of_atom = nullptr;
     w.atom_of_row = nullptr;
     w.seg_off = nullptr;
