@@ -365,6 +365,18 @@ __device__ __forceinline__ float dd_rel(float xjh, float xjl, float sh, float sl
 }
 
 constexpr int kNbWarps = 8;
+constexpr int kNbQueue = 64;   // candidates within the filter band awaiting the exact test
+
+// per-warp tables of the candidate loop: the current batch of 32 window cells (candidate
+// offsets, first slot, image shift hi with the packed image code, shift lo) and the queue of
+// filtered candidates (slot in cell order, cell of the batch)
+struct NbWarpTables {
+    int pre[33];
+    int beg[32];
+    float4 shA[32];
+    float4 shB[32];
+    int4 queue[kNbQueue];
+};
 
 // Rare paths with FP64 arithmetic, kept out of line: GB300 runs FP64 at 1/64 of the FP32
 // rate, and the hot loop must not carry (even predicated-off) FP64 instructions.
@@ -394,7 +406,8 @@ __device__ __noinline__ bool retest_fp64(float4 xjh, float4 xjl, Shift6 sh, floa
     return (rx * rx + ry * ry + rz * rz) < rc2d;
 }
 
-__global__ void __launch_bounds__(kNbWarps * 32)
+// 4 CTAs of 8 warps per SM (64 registers): the search waits on its candidate loads
+__global__ void __launch_bounds__(kNbWarps * 32, 4)
 k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__ geom,
             const int32_t* __restrict__ atom_cfg, const int32_t* __restrict__ atom_cell,
             const int64_t* __restrict__ cell_start, const int32_t* __restrict__ cell_atoms,
@@ -404,6 +417,7 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
             int2* __restrict__ nb_idx, float4* __restrict__ nb_vlo, DevStatus* st)
 {
     extern __shared__ unsigned char smem_raw[];
+    __shared__ NbWarpTables nb_tables[kNbWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* svec = reinterpret_cast<float4*>(smem_raw) + (size_t)warp * cap;
     int2* sidx = reinterpret_cast<int2*>(reinterpret_cast<float4*>(smem_raw) + (size_t)kNbWarps * cap) + (size_t)warp * cap;
@@ -434,13 +448,54 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
     const unsigned lt = (1u << lane) - 1u;
     int count = 0;
     // The window of (2K+1)^3 cells around the atom's cell, 32 cells at a time (one per lane):
-    // each lane resolves its cell (periodic wrap, image shift, atom range), a warp scan gives
-    // every cell's offset in the concatenated candidate list, and the lanes then take the
-    // candidates 32 at a time, each finding its cell by a binary search over the lanes'
-    // offsets.  Cells are visited in the same order as a nested (d0, d1, d2) loop, atoms in
-    // cell order, so the neighbour order is deterministic.
+    // each lane resolves its cell (periodic wrap, image shift, atom range) into the warp's cell
+    // table, a warp scan gives every cell's offset in the concatenated candidate list, and the
+    // lanes take the candidates 32 at a time, each finding its cell by a binary search over the
+    // offsets.  The filter on the FP32 hi parts (within rc + 0.01 A) is all a candidate costs;
+    // those that pass go to a per-warp queue, and only the queue's entries, 32 at a time, get
+    // the double-float relative vector, the cutoff test and the output.  Cells are visited in
+    // the order of a nested (d0, d1, d2) loop, atoms in cell order, and the queue keeps that
+    // order, so the neighbour order is deterministic.
+    NbWarpTables& tb = nb_tables[warp];
     const int W1 = 2 * g.K[1] + 1, W2 = 2 * g.K[2] + 1;
     const int nwin = (2 * g.K[0] + 1) * W1 * W2;
+    int qhead = 0, qtail = 0;
+    // dense round over queue entries qhead .. qhead + m - 1
+    auto process = [&](int m) {
+        bool in = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+        int j = -1, tc = 0, spj = 0;
+        if (lane < m) {
+            const int4 e = tb.queue[(qhead + lane) & (kNbQueue - 1)];
+            j = cell_atoms[e.x];
+            const float4 xjh = pos_hi_s[e.x], xjl = pos_lo_s[e.x];
+            const float4 ta = tb.shA[e.y], tbl = tb.shB[e.y];
+            tc = __float_as_int(ta.w);
+            spj = __float_as_int(xjh.w);
+            dx = dd_rel(xjh.x, xjl.x, ta.x, tbl.x, xih.x, xil.x, lx);
+            dy = dd_rel(xjh.y, xjl.y, ta.y, tbl.y, xih.y, xil.y, ly);
+            dz = dd_rel(xjh.z, xjl.z, ta.z, tbl.z, xih.z, xil.z, lz);
+            r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+            if (fabsf(r2 - rc2) <= 2e-6f * rc2) {
+                const Shift6 cs{ta.x, ta.y, ta.z, tbl.x, tbl.y, tbl.z};
+                in = retest_fp64(xjh, xjl, cs, xih, xil, rc2d);   // FP64 near the cutoff
+            } else {
+                in = r2 < rc2;
+            }
+            if (in && r2 == 0.f) { set_status(st, PANNA_ERR_BAD_INPUT, (int)i); in = false; }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int pos = count + __popc(mask & lt);
+            if (pos < cap) {
+                svec[pos] = make_float4(dx, dy, dz, sqrtf(r2));
+                sidx[pos] = make_int2(j, tc | (spj << 24));
+                if (nb_vlo) svlo[pos] = make_float4(lx, ly, lz, 0.f);
+            }
+        }
+        count += __popc(mask);
+        qhead += m;
+    };
     for (int cb = 0; cb < nwin; cb += 32) {
         const int wc = cb + lane;
         int cnt = 0, tcode = 0;
@@ -477,66 +532,45 @@ k_neighbors(int64_t N, int S, double rc_d, float rc, const CfgGeom* __restrict__
             const int t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        const int pre = incl - cnt;
         const int total = __shfl_sync(0xffffffffu, incl, 31);
+        tb.pre[lane] = incl - cnt;
+        tb.beg[lane] = (int)beg;
+        tb.shA[lane] = make_float4(sh.h0, sh.h1, sh.h2, __int_as_float(tcode));
+        tb.shB[lane] = make_float4(sh.l0, sh.l1, sh.l2, 0.f);
+        __syncwarp();
         for (int base = 0; base < total; base += 32) {
             const int q = base + lane;
-            // the cell slot of candidate q: the last lane whose offset is <= q (empty cells
-            // share an offset with the next one and lose the search)
-            int sl = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int pr = __shfl_sync(0xffffffffu, pre, sl + step);
-                if (pr <= q) sl += step;
-            }
-            const int pre_s = __shfl_sync(0xffffffffu, pre, sl);
-            const int64_t beg_s = __shfl_sync(0xffffffffu, beg, sl);
-            const int tc = __shfl_sync(0xffffffffu, tcode, sl);
-            Shift6 cs;
-            cs.h0 = __shfl_sync(0xffffffffu, sh.h0, sl);
-            cs.h1 = __shfl_sync(0xffffffffu, sh.h1, sl);
-            cs.h2 = __shfl_sync(0xffffffffu, sh.h2, sl);
-            cs.l0 = __shfl_sync(0xffffffffu, sh.l0, sl);
-            cs.l1 = __shfl_sync(0xffffffffu, sh.l1, sl);
-            cs.l2 = __shfl_sync(0xffffffffu, sh.l2, sl);
-            bool in = false;
-            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-            int j = -1, spj = 0;
+            bool band = false;
+            int slot = 0, sl = 0;
             if (q < total) {
-                const int64_t slot = beg_s + (q - pre_s);
-                j = cell_atoms[slot];
+                // the cell of candidate q: the last cell whose offset is <= q (empty cells share
+                // an offset with the next one and lose the search)
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (tb.pre[sl + step] <= q) sl += step;
+                slot = tb.beg[sl] + (q - tb.pre[sl]);
                 const float4 xjh = pos_hi_s[slot];
-                spj = __float_as_int(xjh.w);
-                const float fx = (xjh.x + cs.h0) - xih.x;
-                const float fy = (xjh.y + cs.h1) - xih.y;
-                const float fz = (xjh.z + cs.h2) - xih.z;
+                const float4 ta = tb.shA[sl];
+                const float fx = (xjh.x + ta.x) - xih.x;
+                const float fy = (xjh.y + ta.y) - xih.y;
+                const float fz = (xjh.z + ta.z) - xih.z;
                 const float f2 = fx * fx + fy * fy + fz * fz;
-                const bool self_image = (tc & 0xffffff) == pack_meta(0, 0, 0, 0);
-                if (f2 < band2 && !(self_image && j == (int)i)) {
-                    const float4 xjl = pos_lo_s[slot];
-                    dx = dd_rel(xjh.x, xjl.x, cs.h0, cs.l0, xih.x, xil.x, lx);
-                    dy = dd_rel(xjh.y, xjl.y, cs.h1, cs.l1, xih.y, xil.y, ly);
-                    dz = dd_rel(xjh.z, xjl.z, cs.h2, cs.l2, xih.z, xil.z, lz);
-                    r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
-                    if (fabsf(r2 - rc2) <= 2e-6f * rc2) {
-                        in = retest_fp64(xjh, xjl, cs, xih, xil, rc2d);   // FP64 near the cutoff
-                    } else {
-                        in = r2 < rc2;
-                    }
-                    if (in && r2 == 0.f) { set_status(st, PANNA_ERR_BAD_INPUT, (int)i); in = false; }
-                }
+                // the atom itself (unshifted image, its own slot in cell order) is no neighbour
+                const bool self = (__float_as_int(ta.w) & 0xffffff) == pack_meta(0, 0, 0, 0) && slot == (int)gw;
+                band = f2 < band2 && !self;
             }
-            const unsigned mask = __ballot_sync(0xffffffffu, in);
-            if (in) {
-                const int pos = count + __popc(mask & lt);
-                if (pos < cap) {
-                    svec[pos] = make_float4(dx, dy, dz, sqrtf(r2));
-                    sidx[pos] = make_int2(j, tc | (spj << 24));
-                    if (nb_vlo) svlo[pos] = make_float4(lx, ly, lz, 0.f);
-                }
+            const unsigned bm = __ballot_sync(0xffffffffu, band);
+            if (band) tb.queue[(qtail + __popc(bm & lt)) & (kNbQueue - 1)] = make_int4(slot, sl, 0, 0);
+            qtail += __popc(bm);
+            __syncwarp();
+            if (qtail - qhead >= 32) {
+                process(32);
+                __syncwarp();
             }
-            count += __popc(mask);
         }
+        // the next batch of cells rewrites the table: finish the queue first
+        if (qtail > qhead) process(qtail - qhead);
+        __syncwarp();
     }
     if (count > cap && lane == 0) {
         atomicMax(&st->need_cap, count);
