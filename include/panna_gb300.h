@@ -196,6 +196,9 @@ int32_t panna_neighbor_capacity(const panna_ctx* ctx);
 panna_status panna_set_async(panna_ctx* ctx, int32_t async);
 
 /*
+ * With the BF16 networks (and mode 2 below) the compensated descriptor and the diagonal-order
+ * adjoint use their fast forms (hardware approximations without Newton steps, y^zeta from the
+ * hardware log2): about 1e-5 relative per term, below the 2^-16 of the BF16 hi + lo operand rows.
  * Arithmetic of the angular descriptor terms in kernel variants 0 and 1 (descriptor, adjoint,
  * JVP; the compensated variants 2..5 always evaluate the angle from the FP32 relative vectors,
  * t_m = 1 - y_m from the half angles and y^zeta from a series of log(1 - t): far more accurate

@@ -471,7 +471,7 @@ panna_status run_once(panna_ctx* c, const panna_system* sys, const Request& rq, 
         const bool tcp = rq.prec == PANNA_MLP_BF16 || rq.prec == PANNA_MLP_BF16_FAST;
         __nv_bfloat16 *gh = nullptr, *gl = nullptr;
         if (tcp) tc_g16(c->plan, N, rq.prec == PANNA_MLP_BF16, L.tc_ws, &gh, &gl);
-        cudaError_t eb = gh ? launch_descriptor_bf16(L.w, c->d, gh, gl, L.w.row_of_atom, v, s, &nl)
+        cudaError_t eb = gh ? launch_descriptor_bf16(L.w, c->d, gh, gl, L.w.row_of_atom, v, s, &nl, !acc)
                             : cudaErrorNotSupported;
         if (eb == cudaErrorNotSupported) {
             CU(launch_descriptor(L.w, c->d, L.G, L.w.row_of_atom, acc, s, &nl, v));

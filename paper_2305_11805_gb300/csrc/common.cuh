@@ -151,8 +151,10 @@ cudaError_t launch_adjoint(const Work& w, const DescDev& d, const float* g_rows,
 // descriptor rows written straight into the BF16 hi (+ lo) operands of the tensor-core networks
 // (compensated variants 2..4 of the modified term, batches that need no atom splits);
 // cudaErrorNotSupported otherwise (then write FP32 rows and convert)
+// fast: the approximate-intrinsic forms (no Newton steps, log2-based powers), enough for BF16
+// networks whose operand rows hold about 16 significant bits
 cudaError_t launch_descriptor_bf16(const Work& w, const DescDev& d, __nv_bfloat16* Gh, __nv_bfloat16* Gl,
-                                   const int32_t* row_map, int variant, cudaStream_t s, int* launches);
+                                   const int32_t* row_map, int variant, cudaStream_t s, int* launches, bool fast);
 cudaError_t launch_jvp(const Work& w, const DescDev& d, const float* u, float* wdot_rows, bool acc, cudaStream_t s,
                        int* launches, int variant = 0);
 
