@@ -515,6 +515,7 @@ class Potential:
         Ea = torch.empty(sysd.n_atoms, dtype=torch.float32, device="cuda") if atom_energies else None
         F = torch.empty((sysd.n_atoms, 3), dtype=torch.float32, device="cuda")
         V = torch.empty((sysd.n_cfg, 3, 3), dtype=torch.float64, device="cuda") if virial else None
+        _dev(theta, "float32", self.P, "theta")
         panna_energy_forces(self.ctx, sysd, theta, prec, E, Ea, F, V)
         return E, Ea, F, V
 
@@ -531,6 +532,11 @@ class Potential:
     def param_vjp(self, sysd: DeviceSystem, theta, dE=None, dF=None):
         import torch
         out = torch.empty(self.P, dtype=torch.float32, device="cuda")
+        _dev(theta, "float32", self.P, "theta")
+        if dE is not None:
+            _dev(dE, "float64", sysd.n_cfg, "dE")
+        if dF is not None:
+            _dev(dF, "float32", 3 * sysd.n_atoms, "dF")
         panna_param_vjp(self.ctx, sysd, theta, dE, dF, out)
         return out
 
@@ -540,6 +546,9 @@ class Potential:
         g = torch.empty(self.P, dtype=torch.float32, device="cuda")
         E = torch.empty(sysd.n_cfg, dtype=torch.float64, device="cuda")
         F = torch.empty((sysd.n_atoms, 3), dtype=torch.float32, device="cuda")
+        _dev(theta, "float32", self.P, "theta")
+        _dev(E_ref, "float64", sysd.n_cfg, "E_ref")
+        _dev(F_ref, "float32", 3 * sysd.n_atoms, "F_ref")
         panna_loss_grad(self.ctx, sysd, theta, E_ref, F_ref, w_force, loss, g, E, F)
         return loss, g, E, F
 
