@@ -218,8 +218,8 @@ panna_status panna_set_angular_precision(panna_ctx* ctx, int32_t mode);
 /*
  * Kernel variants and the autotuner.  knob "autotune": 1 (default) = on the first
  * synchronous call for a given problem signature (atoms, configurations, neighbour
- * capacity, precision) time the candidate variants on the caller's stream and keep the
- * fastest; 0 = use a fixed rule (flattened with several species, blocked with one).
+ * capacity, precision) time the candidate variants on the caller's stream (three launches
+ * each) and keep the fastest; 0 = use a fixed rule (see below).
  * knobs "descriptor", "adjoint", "jvp" (the three kernels over angular pairs): -1 (default)
  * = tuned, 0 = pairs by species block (8 warps per CTA), 1 = all pairs of an atom in one
  * flattened range (4 warps per CTA; shared-memory atomics make the sums reproducible to

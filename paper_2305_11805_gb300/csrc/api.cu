@@ -370,7 +370,8 @@ ParamRanges frozen_ranges(const panna_ctx* c)
 // 1 flattened, 2 / 3 / 4 compensated with 32 / 16 / 8 lanes per unit; the adjoint's 4 is the
 // flattened compensated walk and its 5 the diagonal-order walk without shared-memory atomics):
 // measured once per kernel
-// (each variant launched once to warm up, then timed with CUDA events on the caller's stream),
+// (each variant launched once to warm up, then timed over three launches with CUDA events on
+// the caller's stream),
 // then cached.  Asynchronous calls never measure (they may be under stream capture) and use
 // the cached or default choice.
 enum { KV_DESC = 0, KV_ADJ = 1, KV_JVP = 2 };
@@ -409,9 +410,11 @@ int tuned_variant_(panna_ctx* c, const panna_system* sys, int prec, int kind, cu
     const int nv = ext ? 2 : kKindVariants[kind];
     for (int v = 0; v < nv; ++v) launch(v);   // first launches load and configure the kernels
     int best = 0;
+    // three back-to-back launches per variant: the host's launch work then overlaps the kernels
+    // instead of showing up as idle device time in a single short measurement
     for (int v = 0; v < nv; ++v) {
         cudaEventRecord(c->tev[0], s);
-        launch(v);
+        for (int r = 0; r < 3; ++r) launch(v);
         cudaEventRecord(c->tev[1], s);
         cudaEventSynchronize(c->tev[1]);
         cudaEventElapsedTime(&ms[v], c->tev[0], c->tev[1]);
