@@ -4,8 +4,10 @@
 // the reverse pass over forward + tangent (the double backward of the force loss).
 //
 // Rows of species s are seg_off[s]..seg_off[s+1]-1 (device); the tile table maps a
-// CTA to (species, 64-row tile) without the host knowing the species counts, so one
+// CTA to (species, 128-row tile) without the host knowing the species counts, so one
 // launch covers all species and the launch shape depends only on N and S.
+#include <algorithm>
+
 #include "mlp.cuh"
 
 namespace panna {
@@ -63,19 +65,36 @@ __device__ __forceinline__ bool tile_species(int S, const int32_t* tile_start, i
 // PRO_DACT: A[r][k] is multiplied by act'(Zp[r][k]) on load (layer activation la.pact).
 // EPI_FWD:  C = Z = acc + b, C2 = act(Z);  EPI_TAN: C = acc, C2 = act'(Ze) * acc.
 //
-// 128 x 128 tile per CTA of 256 threads; each thread owns 8 x 8 outputs (rows ty*4 + {0..3}
-// and 64 + ty*4 + {0..3}, likewise columns), so its shared-memory reads are float4 and
-// conflict-free.  K advances 8 at a time through double-buffered shared tiles; the next
-// tile's global loads are issued before the current tile's FMAs.  Every output is one FMA
-// chain in k order, as in a plain dot product.
+// BM x 128 tile per CTA of 256 threads, BM = 128 or 64; each thread owns BM/16 x 8 outputs
+// (rows ty*4 + {0..3}, and 64 + ty*4 + {0..3} when BM = 128; columns tx*4 + {0..3} and
+// 64 + tx*4 + {0..3}), so its shared-memory reads are float4 and conflict-free.  K advances 8
+// at a time through double-buffered shared tiles; the next tile's global loads are issued
+// before the current tile's FMAs.  Every output is one FMA chain in k order, as in a plain
+// dot product, whatever BM.  The 64-row form splits each 128-row tile of the tile table in
+// two (CTA x -> tile x/2, half x%2) and serves grids that would leave SMs with one CTA.
 struct GemmLoad { float a[4], b[4]; };
 
-template <bool B_TRANS, int PRO>
+template <bool B_TRANS, int PRO, int BM>
 __device__ __forceinline__ void gemm_fetch(const LayerArgs& la, int s, const float* __restrict__ A, int lda,
                                            const float* __restrict__ Zp, int ldp, const float* __restrict__ W,
                                            int K, int N, int r0, int rend, int n0, int k0, int tid, GemmLoad& g)
 {
-    {   // A tile: 128 rows x 8 k; thread -> row tid/2, k quad (tid&1)*4
+    if (BM == 64) {   // A tile: 64 rows x 8 k; thread -> row tid/4, k pair (tid&3)*2
+        const int r = r0 + (tid >> 2), kq = k0 + (tid & 3) * 2;
+        const bool vec = ((reinterpret_cast<uintptr_t>(A) & 7) == 0) && (lda & 1) == 0;
+        if (vec && r < rend && kq + 1 < K) {
+            const float2 v = *reinterpret_cast<const float2*>(A + (size_t)r * lda + kq);
+            g.a[0] = v.x; g.a[1] = v.y;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) g.a[j] = (r < rend && kq + j < K) ? A[(size_t)r * lda + kq + j] : 0.f;
+        }
+        if (PRO == PRO_DACT && r < rend) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (kq + j < K) g.a[j] *= act_d1(la.pact[s], Zp[(size_t)r * ldp + kq + j]);
+        }
+    } else {   // A tile: 128 rows x 8 k; thread -> row tid/2, k quad (tid&1)*4
         const int r = r0 + (tid >> 1), kq = k0 + (tid & 1) * 4;
         const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda & 3) == 0;
         if (vec && r < rend && kq + 3 < K) {
@@ -115,21 +134,28 @@ __device__ __forceinline__ void gemm_fetch(const LayerArgs& la, int s, const flo
     }
 }
 
-template <bool B_TRANS>
+template <bool B_TRANS, int BM>
 __device__ __forceinline__ void gemm_stash(const GemmLoad& g, float (*As)[kGM], float (*Bs)[kGN], int tid)
 {
-    const int m = tid >> 1, kq = (tid & 1) * 4;
+    if (BM == 64) {
+        const int m = tid >> 2, kq = (tid & 3) * 2;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) As[kq + j][m] = g.a[j];
-    if (B_TRANS) {
+        for (int j = 0; j < 2; ++j) As[kq + j][m] = g.a[j];
+    } else {
+        const int m = tid >> 1, kq = (tid & 1) * 4;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) Bs[kq + j][m] = g.b[j];
+        for (int j = 0; j < 4; ++j) As[kq + j][m] = g.a[j];
+    }
+    if (B_TRANS) {   // 128 n x 8 k: n tid/2, k quad (tid&1)*4
+        const int n = tid >> 1, kq = (tid & 1) * 4;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Bs[kq + j][n] = g.b[j];
     } else {
         *reinterpret_cast<float4*>(&Bs[tid >> 5][(tid & 31) * 4]) = make_float4(g.b[0], g.b[1], g.b[2], g.b[3]);
     }
 }
 
-template <bool B_TRANS, int PRO, int EPI>
+template <bool B_TRANS, int PRO, int EPI, int BM>
 __global__ void __launch_bounds__(256, 2)
 k_gemm(LayerArgs la, const float* __restrict__ theta, const int32_t* __restrict__ seg_off,
        const int32_t* __restrict__ tile_start, const float* __restrict__ A, int lda,
@@ -138,42 +164,46 @@ k_gemm(LayerArgs la, const float* __restrict__ theta, const int32_t* __restrict_
 {
     __shared__ __align__(16) float As[2][kGK][kGM];
     __shared__ __align__(16) float Bs[2][kGK][kGN];
+    constexpr int P = BM / 16;   // output rows per thread
+    const int tile = BM == 128 ? (int)blockIdx.x : (int)(blockIdx.x >> 1);
     int s;
-    if (!tile_species(la.S, tile_start, blockIdx.x, s)) return;
+    if (!tile_species(la.S, tile_start, tile, s)) return;
     const int K = la.K[s], N = la.N[s];
     const int n0 = blockIdx.y * kGN;
     if (n0 >= N) return;
-    const int r0 = seg_off[s] + (blockIdx.x - tile_start[s]) * kGM;
+    const int r0 = seg_off[s] + (tile - tile_start[s]) * kGM + (BM == 128 ? 0 : (int)(blockIdx.x & 1) * 64);
     const int rend = seg_off[s + 1];
+    if (r0 >= rend) return;   // second half of a species' last tile
     const float* W = theta + la.w_off[s];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    float acc[8][8];
+    float acc[P][8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < P; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
     GemmLoad g;
-    gemm_fetch<B_TRANS, PRO>(la, s, A, lda, Zp, ldp, W, K, N, r0, rend, n0, 0, tid, g);
-    gemm_stash<B_TRANS>(g, As[0], Bs[0], tid);
+    gemm_fetch<B_TRANS, PRO, BM>(la, s, A, lda, Zp, ldp, W, K, N, r0, rend, n0, 0, tid, g);
+    gemm_stash<B_TRANS, BM>(g, As[0], Bs[0], tid);
     __syncthreads();
     const int nk = (K + kGK - 1) / kGK;
     for (int t = 0; t < nk; ++t) {
         const int cur = t & 1;
-        if (t + 1 < nk) gemm_fetch<B_TRANS, PRO>(la, s, A, lda, Zp, ldp, W, K, N, r0, rend, n0, (t + 1) * kGK, tid, g);
+        if (t + 1 < nk)
+            gemm_fetch<B_TRANS, PRO, BM>(la, s, A, lda, Zp, ldp, W, K, N, r0, rend, n0, (t + 1) * kGK, tid, g);
 #pragma unroll
         for (int kk = 0; kk < kGK; ++kk) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+            const float4 a1 = BM == 128 ? *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]) : a0;
             const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
             const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int p = 0; p < 8; ++p)
+            for (int p = 0; p < P; ++p)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
         }
-        if (t + 1 < nk) gemm_stash<B_TRANS>(g, As[cur ^ 1], Bs[cur ^ 1], tid);
+        if (t + 1 < nk) gemm_stash<B_TRANS, BM>(g, As[cur ^ 1], Bs[cur ^ 1], tid);
         __syncthreads();
     }
     // epilogue: each thread's 4 consecutive columns go out as one float4 where the row start
@@ -182,7 +212,7 @@ k_gemm(LayerArgs la, const float* __restrict__ theta, const int32_t* __restrict_
     const bool vst = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc & 3) == 0 &&
                      (EPI == EPI_STORE || ((reinterpret_cast<uintptr_t>(C2) & 15) == 0));
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
+    for (int p = 0; p < P; ++p) {
         const int r = r0 + (p < 4 ? ty * 4 + p : 64 + ty * 4 + p - 4);
         if (r >= rend) continue;
 #pragma unroll
@@ -357,6 +387,43 @@ static dim3 gemm_grid(const MlpPlan& p, int64_t N, int n_max)
     return dim3((unsigned)((N + kGM - 1) / kGM + p.S), (unsigned)((n_max + kGN - 1) / kGN), 1);
 }
 
+static int device_sms()
+{
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n_sm = v;
+        else
+            return 1;
+    }
+    return n_sm;
+}
+
+// One layer GEMM: the 64-row form (twice the CTAs, twice the resident warps per SM) when the
+// 128-row grid leaves SMs with fewer than two CTAs and the reduction is short (K <= 256);
+// else 128-row tiles.  On 17,780 rows the 64-row form took the K = 128 layers from 12.3 to
+// 10.1 us but the K = 768 first layer from 109 to 145 us (more weight-tile traffic and fewer
+// FMAs per shared-memory load), so long reductions keep the 128-row tiles.
+template <bool B_TRANS, int PRO, int EPI>
+static void launch_gemm(const MlpPlan& p, int64_t N, int n_max, cudaStream_t s, const LayerArgs& la,
+                        const float* theta, const int32_t* seg_off, const int32_t* tile_start, const float* A,
+                        int lda, const float* Zp, int ldp, float* C, int ldc, float* C2, const float* Ze, int lde)
+{
+    dim3 g = gemm_grid(p, N, n_max);
+    int kmax = 0;
+    for (int q = 0; q < la.S; ++q) kmax = std::max(kmax, la.K[q]);
+    if ((int64_t)g.x * g.y < 2 * (int64_t)device_sms() && kmax <= 256) {
+        g.x *= 2;
+        k_gemm<B_TRANS, PRO, EPI, 64><<<g, 256, 0, s>>>(la, theta, seg_off, tile_start, A, lda, Zp, ldp, C, ldc,
+                                                        C2, Ze, lde);
+    } else {
+        k_gemm<B_TRANS, PRO, EPI, 128><<<g, 256, 0, s>>>(la, theta, seg_off, tile_start, A, lda, Zp, ldp, C, ldc,
+                                                         C2, Ze, lde);
+    }
+}
+
 cudaError_t mlp_tiles(const MlpPlan& p, const int32_t* seg_off, int32_t* tile_start, cudaStream_t s, int* launches)
 {
     k_tiles<<<1, 32, 0, s>>>(p.S, seg_off, tile_start);
@@ -371,9 +438,8 @@ cudaError_t mlp_forward(const MlpPlan& p, const MlpBuffers& b, const float* thet
         LayerArgs la = layer_args(p, l, false);
         const float* Ain = l == 0 ? b.G : b.A[l];
         const int lda = p.ld[l];
-        k_gemm<true, PRO_NONE, EPI_FWD><<<gemm_grid(p, N, p.ld[l + 1]), 256, 0, s>>>(
-            la, theta, b.seg_off, b.tile_start, Ain, lda, nullptr, 0, b.Z[l + 1], p.ld[l + 1], b.A[l + 1],
-            nullptr, 0);
+        launch_gemm<true, PRO_NONE, EPI_FWD>(p, N, p.ld[l + 1], s, la, theta, b.seg_off, b.tile_start, Ain, lda,
+                                             nullptr, 0, b.Z[l + 1], p.ld[l + 1], b.A[l + 1], nullptr, 0);
         ++*launches;
     }
     return cudaGetLastError();
@@ -394,9 +460,8 @@ cudaError_t mlp_input_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
         LayerArgs la = layer_args(p, l, true);
         float* out = l == 0 ? g : nxt;
         const int ldo = p.ld[l];
-        k_gemm<false, PRO_DACT, EPI_STORE><<<gemm_grid(p, N, p.ld[l]), 256, 0, s>>>(
-            la, theta, b.seg_off, b.tile_start, cur, p.ld[l + 1], b.Z[l + 1], p.ld[l + 1], out, ldo, nullptr,
-            nullptr, 0);
+        launch_gemm<false, PRO_DACT, EPI_STORE>(p, N, p.ld[l], s, la, theta, b.seg_off, b.tile_start, cur,
+                                                p.ld[l + 1], b.Z[l + 1], p.ld[l + 1], out, ldo, nullptr, nullptr, 0);
         ++*launches;
         float* t = cur; cur = out; nxt = t;
     }
@@ -412,9 +477,9 @@ cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
     for (int l = tan_tc ? 1 : 0; l < p.L && part != MLP_GRAD_REVERSE_SEEDED; ++l) {
         LayerArgs la = layer_args(p, l, false);
         const float* Ain = l == 0 ? wdot : b.Ad[l];
-        k_gemm<true, PRO_NONE, EPI_TAN><<<gemm_grid(p, N, p.ld[l + 1]), 256, 0, s>>>(
-            la, theta, b.seg_off, b.tile_start, Ain, p.ld[l], nullptr, 0, b.Zd[l + 1], p.ld[l + 1], b.Ad[l + 1],
-            b.Z[l + 1], p.ld[l + 1]);
+        launch_gemm<true, PRO_NONE, EPI_TAN>(p, N, p.ld[l + 1], s, la, theta, b.seg_off, b.tile_start, Ain,
+                                             p.ld[l], nullptr, 0, b.Zd[l + 1], p.ld[l + 1], b.Ad[l + 1], b.Z[l + 1],
+                                             p.ld[l + 1]);
         ++*launches;
     }
     if (part == MLP_GRAD_TANGENT) return cudaGetLastError();
@@ -446,10 +511,10 @@ cudaError_t mlp_param_grad(const MlpPlan& p, const MlpBuffers& b, const float* t
         if (l > 0) {
             // abar_{l} = Zb W_{l+1}, adotbar_{l} = Zdb W_{l+1}
             LayerArgs la = layer_args(p, l, true);
-            k_gemm<false, PRO_NONE, EPI_STORE><<<gemm_grid(p, N, p.ld[l]), 256, 0, s>>>(
-                la, theta, b.seg_off, b.tile_start, b.Zb, ldl, nullptr, 0, b.Ab, p.ld[l], nullptr, nullptr, 0);
-            k_gemm<false, PRO_NONE, EPI_STORE><<<gemm_grid(p, N, p.ld[l]), 256, 0, s>>>(
-                la, theta, b.seg_off, b.tile_start, b.Zdb, ldl, nullptr, 0, b.Adb, p.ld[l], nullptr, nullptr, 0);
+            launch_gemm<false, PRO_NONE, EPI_STORE>(p, N, p.ld[l], s, la, theta, b.seg_off, b.tile_start, b.Zb,
+                                                    ldl, nullptr, 0, b.Ab, p.ld[l], nullptr, nullptr, 0);
+            launch_gemm<false, PRO_NONE, EPI_STORE>(p, N, p.ld[l], s, la, theta, b.seg_off, b.tile_start, b.Zdb,
+                                                    ldl, nullptr, 0, b.Adb, p.ld[l], nullptr, nullptr, 0);
             *launches += 2;
         }
     }

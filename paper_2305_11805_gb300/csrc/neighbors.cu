@@ -319,26 +319,92 @@ __global__ void k_scatter(int64_t N, const int32_t* __restrict__ atom_cfg, const
 
 // atoms of each cell sorted by index; with pos_hi_s / pos_lo_s, the folded positions copied in
 // that cell order (the candidate loop of the search then reads a candidate's position by its
-// slot, not through its atom index)
-__global__ void k_sort_cells(int64_t ncells, const int64_t* __restrict__ cell_start, int32_t* __restrict__ cell_atoms,
-                             const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo,
-                             float4* __restrict__ pos_hi_s, float4* __restrict__ pos_lo_s)
+// slot, not through its atom index).  One warp per 32 consecutive cells: the lanes read the 32
+// cells' ranges at once and the warp sorts the non-empty ones in turn.  A cell of up to
+// 32 * kSortPer atoms is held in registers and each atom goes to slot b + (number of the cell's
+// atoms with a smaller index), the indices being distinct; larger cells are sorted by insertion
+// on one lane.
+constexpr int kSortWarps = 8;
+constexpr int kSortPer = 4;
+
+__device__ __forceinline__ void sort_cell(int64_t b, int64_t e, int lane, int32_t* __restrict__ cell_atoms,
+                                          const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo,
+                                          float4* __restrict__ pos_hi_s, float4* __restrict__ pos_lo_s)
 {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncells) return;
-    int64_t b = cell_start[c], e = cell_start[c + 1];
-    for (int64_t k = b + 1; k < e; ++k) {
-        int32_t v = cell_atoms[k];
-        int64_t q = k - 1;
-        while (q >= b && cell_atoms[q] > v) { cell_atoms[q + 1] = cell_atoms[q]; --q; }
-        cell_atoms[q + 1] = v;
+    const int64_t n = e - b;
+    if (n <= 32 * kSortPer) {
+        int32_t v[kSortPer];
+        int rank[kSortPer];
+#pragma unroll
+        for (int t = 0; t < kSortPer; ++t) {
+            const int64_t k = lane + 32 * t;
+            v[t] = k < n ? cell_atoms[b + k] : INT32_MAX;
+            rank[t] = 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortPer; ++u) {
+            const int64_t left = n - 32 * u;
+            const int m = left < 32 ? (int)left : 32;   // atoms held in the lanes' v[u]
+            if (m <= 0) break;
+            for (int src = 0; src < m; ++src) {
+                const int32_t y = __shfl_sync(0xffffffffu, v[u], src);
+#pragma unroll
+                for (int t = 0; t < kSortPer; ++t) rank[t] += y < v[t] ? 1 : 0;
+            }
+        }
+        __syncwarp();   // every lane has read its atoms before any slot is rewritten
+#pragma unroll
+        for (int t = 0; t < kSortPer; ++t) {
+            if (lane + 32 * t >= n) continue;
+            const int64_t k = b + rank[t];
+            cell_atoms[k] = v[t];
+            if (pos_hi_s) {
+                pos_hi_s[k] = pos_hi[v[t]];
+                pos_lo_s[k] = pos_lo[v[t]];
+            }
+        }
+        __syncwarp();
+        return;
     }
+    if (lane == 0) {
+        for (int64_t k = b + 1; k < e; ++k) {
+            int32_t v = cell_atoms[k];
+            int64_t q = k - 1;
+            while (q >= b && cell_atoms[q] > v) { cell_atoms[q + 1] = cell_atoms[q]; --q; }
+            cell_atoms[q + 1] = v;
+        }
+    }
+    __syncwarp();   // lane 0's writes are visible to the warp after this
     if (pos_hi_s) {
-        for (int64_t k = b; k < e; ++k) {
+        for (int64_t k = b + lane; k < e; k += 32) {
             const int32_t j = cell_atoms[k];
             pos_hi_s[k] = pos_hi[j];
             pos_lo_s[k] = pos_lo[j];
         }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_sort_cells(int64_t ncells, const int64_t* __restrict__ cell_start, int32_t* __restrict__ cell_atoms,
+             const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo,
+             float4* __restrict__ pos_hi_s, float4* __restrict__ pos_lo_s)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t c0 = ((int64_t)blockIdx.x * kSortWarps + (threadIdx.x >> 5)) * 32;
+    if (c0 >= ncells) return;
+    const int64_t cl = c0 + lane;
+    int64_t bl = 0, el = 0;
+    if (cl < ncells) {
+        bl = cell_start[cl];
+        el = cell_start[cl + 1];
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, el > bl);
+    while (todo) {
+        const int i = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t b = __shfl_sync(0xffffffffu, bl, i), e = __shfl_sync(0xffffffffu, el, i);
+        sort_cell(b, e, lane, cell_atoms, pos_hi, pos_lo, pos_hi_s, pos_lo_s);
     }
 }
 
@@ -778,8 +844,11 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
     e = exclusive_scan_i64(w.cell_count, w.cell_start, w.cap_cells, w.scan_tmp, s, launches);
     if (e != cudaSuccess) return e;
     k_scatter<<<nbA, 256, 0, s>>>(N, w.atom_cfg, w.atom_cell, w.geom, w.cell_start, w.cell_fill, w.cell_atoms);
-    k_sort_cells<<<(unsigned)((w.cap_cells + 255) / 256), 256, 0, s>>>(w.cap_cells, w.cell_start, w.cell_atoms,
-                                                                        w.pos_hi, w.pos_lo, w.pos_hi_s, w.pos_lo_s);
+    {
+        const int64_t warps = (w.cap_cells + 31) / 32;   // one warp per 32 cells
+        k_sort_cells<<<(unsigned)((warps + kSortWarps - 1) / kSortWarps), kSortWarps * 32, 0, s>>>(
+            w.cap_cells, w.cell_start, w.cell_atoms, w.pos_hi, w.pos_lo, w.pos_hi_s, w.pos_lo_s);
+    }
     *launches += 2;
     size_t smem = (size_t)kNbWarps * w.cap * (sizeof(float4) + sizeof(int2) + (w.nb_vlo ? sizeof(float4) : 0));
     e = cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
