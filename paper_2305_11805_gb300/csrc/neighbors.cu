@@ -16,6 +16,8 @@
 //   k_species_*    stable counting sort of atoms by species (network row order).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace panna {
@@ -319,13 +321,14 @@ __global__ void k_scatter(int64_t N, const int32_t* __restrict__ atom_cfg, const
 
 // atoms of each cell sorted by index; with pos_hi_s / pos_lo_s, the folded positions copied in
 // that cell order (the candidate loop of the search then reads a candidate's position by its
-// slot, not through its atom index).  One warp per 32 consecutive cells: the lanes read the 32
-// cells' ranges at once and the warp sorts the non-empty ones in turn.  A cell of up to
-// 32 * kSortPer atoms is held in registers and each atom goes to slot b + (number of the cell's
-// atoms with a smaller index), the indices being distinct; larger cells are sorted by insertion
-// on one lane.
+// slot, not through its atom index).  Resident warps take the cells in use (the configurations'
+// grids, read from the last configuration's geometry; the cell slots past them are empty) one
+// cell per warp in turn.  A cell of up to 32 * kSortPer atoms is held in registers and each atom
+// goes to slot b + (number of the cell's atoms with a smaller index), the indices being
+// distinct; larger cells are sorted by insertion on one lane.
 constexpr int kSortWarps = 8;
 constexpr int kSortPer = 4;
+constexpr int64_t kSortMaxWarps = 152 * 256;   // enough warps to fill every SM several times
 
 __device__ __forceinline__ void sort_cell(int64_t b, int64_t e, int lane, int32_t* __restrict__ cell_atoms,
                                           const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo,
@@ -386,25 +389,17 @@ __device__ __forceinline__ void sort_cell(int64_t b, int64_t e, int lane, int32_
 }
 
 __global__ void __launch_bounds__(kSortWarps * 32)
-k_sort_cells(int64_t ncells, const int64_t* __restrict__ cell_start, int32_t* __restrict__ cell_atoms,
-             const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo,
+k_sort_cells(int64_t C, const CfgGeom* __restrict__ geom, int64_t ncells, const int64_t* __restrict__ cell_start,
+             int32_t* __restrict__ cell_atoms, const float4* __restrict__ pos_hi, const float4* __restrict__ pos_lo,
              float4* __restrict__ pos_hi_s, float4* __restrict__ pos_lo_s)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t c0 = ((int64_t)blockIdx.x * kSortWarps + (threadIdx.x >> 5)) * 32;
-    if (c0 >= ncells) return;
-    const int64_t cl = c0 + lane;
-    int64_t bl = 0, el = 0;
-    if (cl < ncells) {
-        bl = cell_start[cl];
-        el = cell_start[cl + 1];
-    }
-    unsigned todo = __ballot_sync(0xffffffffu, el > bl);
-    while (todo) {
-        const int i = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int64_t b = __shfl_sync(0xffffffffu, bl, i), e = __shfl_sync(0xffffffffu, el, i);
-        sort_cell(b, e, lane, cell_atoms, pos_hi, pos_lo, pos_hi_s, pos_lo_s);
+    int64_t used = geom[C - 1].cell_base + geom[C - 1].ncells;
+    if (used > ncells) used = ncells;
+    const int64_t stride = (int64_t)gridDim.x * kSortWarps;
+    for (int64_t c = (int64_t)blockIdx.x * kSortWarps + (threadIdx.x >> 5); c < used; c += stride) {
+        const int64_t b = cell_start[c], e = cell_start[c + 1];
+        if (e > b) sort_cell(b, e, lane, cell_atoms, pos_hi, pos_lo, pos_hi_s, pos_lo_s);
     }
 }
 
@@ -845,9 +840,9 @@ cudaError_t build_neighbors(Work& w, const DescDev& d, cudaStream_t s, int* laun
     if (e != cudaSuccess) return e;
     k_scatter<<<nbA, 256, 0, s>>>(N, w.atom_cfg, w.atom_cell, w.geom, w.cell_start, w.cell_fill, w.cell_atoms);
     {
-        const int64_t warps = (w.cap_cells + 31) / 32;   // one warp per 32 cells
+        const int64_t warps = std::min<int64_t>(w.cap_cells, kSortMaxWarps);
         k_sort_cells<<<(unsigned)((warps + kSortWarps - 1) / kSortWarps), kSortWarps * 32, 0, s>>>(
-            w.cap_cells, w.cell_start, w.cell_atoms, w.pos_hi, w.pos_lo, w.pos_hi_s, w.pos_lo_s);
+            C, w.geom, w.cap_cells, w.cell_start, w.cell_atoms, w.pos_hi, w.pos_lo, w.pos_hi_s, w.pos_lo_s);
     }
     *launches += 2;
     size_t smem = (size_t)kNbWarps * w.cap * (sizeof(float4) + sizeof(int2) + (w.nb_vlo ? sizeof(float4) : 0));
